@@ -1,0 +1,353 @@
+"""Pins for the CPU oracle: each test checks it against something other than itself.
+
+Pins used: the dense operator assembled entry by entry; plane-wave eigenvectors and the closed-form spectrum
+of the periodic (and Bloch-twisted) 7-point Laplacian; separable potentials whose spectrum is a sum of three
+1-D spectra; dense LAPACK eigh; textbook Householder QR; LAPACK's generalised eigh; the LOBPCG special case
+of Section 5.1; Theorem 2; Courant-Fischer bounds on Ritz values.
+"""
+import itertools
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import workloads as wl
+import oracle
+
+
+
+def _rng(seed=0):
+    return np.random.default_rng(seed)
+
+
+# ---------------------------------------------------------------- operator (row a0)
+@pytest.mark.parametrize("N,h", [(3, 1.0), (4, 0.5), (5, 1.0)])
+def test_apply_H_matches_assembled(N, h):
+    rng = _rng(N)
+    V = rng.random(N ** 3)
+    X = rng.standard_normal((N ** 3, 3))
+    A = oracle.assemble_H(V, N, h)
+    assert np.allclose(A, A.T, atol=0)
+    np.testing.assert_allclose(oracle.apply_H(V, N, h, X), A @ X, rtol=0, atol=1e-12)
+
+
+def test_apply_H_bloch_matches_assembled_and_is_hermitian():
+    N, theta = 4, (0.3, 0.7, 1.1)
+    rng = _rng(3)
+    V = rng.random(N ** 3)
+    X = rng.standard_normal((N ** 3, 2)) + 1j * rng.standard_normal((N ** 3, 2))
+    A = oracle.assemble_H(V, N, 1.0, theta)
+    np.testing.assert_allclose(A, A.conj().T, atol=0)
+    np.testing.assert_allclose(oracle.apply_H(V, N, 1.0, X, theta), A @ X, atol=1e-12)
+
+
+def _plane_wave(N, m, theta=(0.0, 0.0, 0.0)):
+    i, j, l = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    phase = sum((2 * np.pi * m[d] + theta[d]) / N * c for d, c in enumerate((i, j, l)))
+    return np.exp(1j * phase).reshape(-1, order="F")
+
+
+@pytest.mark.parametrize("m", [(0, 0, 0), (1, 0, 0), (2, 3, 1), (5, 5, 4)])
+def test_plane_waves_are_eigenvectors(m):
+    # V = 0: eigenvalue sum_d 4 sin^2(pi m_d / N) / h^2
+    N, h = 6, 0.7
+    x = _plane_wave(N, m)
+    lam = sum(4 * np.sin(np.pi * md / N) ** 2 for md in m) / h ** 2
+    np.testing.assert_allclose(oracle.apply_H(np.zeros(N ** 3), N, h, x), lam * x, atol=1e-12)
+
+
+@pytest.mark.parametrize("m", [(0, 0, 0), (1, 2, 3)])
+def test_bloch_plane_waves_are_eigenvectors(m):
+    # psi = exp(i q.r), q_d = (2 pi m_d + theta_d) / N satisfies the twist; eigenvalue sum 4 sin^2(q_d / 2)
+    N, theta = 5, (0.3, 0.7, 1.1)
+    x = _plane_wave(N, m, theta)
+    lam = sum(4 * np.sin((2 * np.pi * m[d] + theta[d]) / (2 * N)) ** 2 for d in range(3))
+    np.testing.assert_allclose(oracle.apply_H(np.zeros(N ** 3), N, 1.0, x, theta), lam * x, atol=1e-12)
+
+
+# ---------------------------------------------------------------- small dense pieces
+def test_cholqr2_equals_textbook_qr():
+    rng = _rng(1)
+    n, k = 400, 12
+    X = rng.standard_normal((n, k)) @ np.diag(np.logspace(0, 5, k)) @ sla.qr(rng.standard_normal((k, k)))[0]
+    Q, R = oracle.cholqr2(X)
+    assert np.allclose(np.triu(R), R)
+    assert np.all(np.diag(R) > 0)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(k), atol=1e-12)
+    np.testing.assert_allclose(Q @ R, X, rtol=0, atol=1e-10 * np.linalg.norm(X))
+    Qh, Rh = np.linalg.qr(X)                 # Householder QR; make diag(R) positive (unique QR)
+    s = np.sign(np.diag(Rh))
+    np.testing.assert_allclose(Q, Qh * s[None, :], atol=1e-10)
+
+
+def test_shifted_cholqr3_handles_breakdown():
+    rng = _rng(2)
+    n, k = 300, 10
+    X = rng.standard_normal((n, k))
+    X[:, -1] = X[:, 0] + 1e-12 * rng.standard_normal(n)     # kappa ~ 1e12: CholQR breaks down
+    with pytest.raises(np.linalg.LinAlgError):
+        oracle.cholqr2(X)
+    Q, R = oracle.shifted_cholqr3(X)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(k), atol=1e-12)
+    np.testing.assert_allclose(Q @ R, X, atol=1e-8)
+
+
+def test_project_removes_span_and_is_idempotent():
+    rng = _rng(4)
+    X = oracle.cholqr2(rng.standard_normal((200, 7)))[0]
+    Y = rng.standard_normal((200, 5))
+    Z = oracle.project(Y, X)
+    assert np.max(np.abs(X.T @ Z)) < 1e-13 * np.linalg.norm(Y)
+    np.testing.assert_allclose(oracle.project(Z, X), Z, atol=1e-13)
+    # the part removed lies in span(X)
+    D = Y - Z
+    np.testing.assert_allclose(X @ (X.T @ D), D, atol=1e-12)
+
+
+def test_theorem2_identity_and_hpd_preconditioner():
+    # x_j* A w_j = r_j* T r_j > 0 with W = (I - XX*) T R, R = (I - XX*) A X (proof of Theorem 2)
+    N = 6
+    rng = _rng(5)
+    V = rng.random(N ** 3)
+    X = oracle.cholqr2(rng.standard_normal((N ** 3, 4)))[0]
+    HX = oracle.apply_H(V, N, 1.0, X)
+    R = oracle.residual(X, HX, X.T @ HX)
+    sigma = 0.3
+    TR = oracle.precondition(R, V, N, 1.0, sigma)
+    W = oracle.project(TR, X)
+    lhs = np.einsum("ij,ij->j", X, oracle.apply_H(V, N, 1.0, W))
+    d = np.maximum(6.0 + V - sigma, 0.1)
+    rhs = np.einsum("ij,ij->j", R, R / d[:, None])
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-10)
+    assert np.all(rhs > 0)
+    # Theorem 2: with P = 0 every alpha_j != 0
+    for j in range(4):
+        CX, CW, CP = oracle.block_coefficients(X[:, j:j + 1], W[:, j:j + 1], None, HX[:, j:j + 1],
+                                               oracle.apply_H(V, N, 1.0, W[:, j:j + 1]), None)
+        assert abs(CX[0, 0]) > 1e-3 and CP is None
+
+
+def test_precondition_floor_keeps_T_positive():
+    V = np.array([-10.0, 0.0, 1.0, 5.0])
+    W = np.ones((4, 1))
+    TW = oracle.precondition(W, V, 1, 1.0, sigma=2.0)      # d = max(6 + V - 2, 0.1)
+    np.testing.assert_allclose(TW[:, 0], 1.0 / np.array([0.1, 4.0, 5.0, 9.0]))
+
+
+@pytest.mark.parametrize("q,with_p", [(1, False), (1, True), (3, True), (4, False)])
+def test_block_coefficients_solve_projev(q, with_p):
+    # eq. projev on S = [X_j, W_j, P_j]: compare with LAPACK's generalised driver
+    N = 5
+    rng = _rng(10 + q)
+    V = rng.random(N ** 3)
+    n = N ** 3
+    X = oracle.cholqr2(rng.standard_normal((n, q)))[0]
+    W = oracle.project(rng.standard_normal((n, q)), X)
+    Pm = oracle.project(rng.standard_normal((n, q)), X) if with_p else None
+    H = lambda Y: oracle.apply_H(V, N, 1.0, Y)
+    CX, CW, CP = oracle.block_coefficients(X, W, Pm, H(X), H(W), None if Pm is None else H(Pm))
+    S = np.hstack([X, W] + ([Pm] if with_p else []))
+    GA, GB = S.T @ H(S), S.T @ S
+    C = np.vstack([CX, CW] + ([CP] if with_p else []))
+    theta_ref = sla.eigh(GA, GB, eigvals_only=True, subset_by_index=[0, q - 1])
+    np.testing.assert_allclose(C.T @ GB @ C, np.eye(q), atol=1e-12)
+    theta = np.linalg.eigvalsh(C.T @ GA @ C)
+    np.testing.assert_allclose(theta, theta_ref, rtol=1e-12, atol=1e-12)
+    # C's columns are eigenvectors: GA C = GB C Theta
+    Th = C.T @ GA @ C
+    np.testing.assert_allclose(GA @ C, GB @ C @ Th, atol=1e-10)
+
+
+def test_block_rr_q1_by_hand():
+    # x _|_ w, both unit norm: the 2x2 problem of eq. (proj2) [[a, b], [b, c]] c = theta c, smallest root
+    n = 64
+    rng = _rng(7)
+    x = rng.standard_normal((n, 1)); x /= np.linalg.norm(x)
+    w = rng.standard_normal((n, 1)); w -= x * (x.T @ w); w /= np.linalg.norm(w)
+    a, b, c = 2.0, 0.5, 5.0
+    # choose "A x", "A w" so that x*Ax = a, x*Aw = b, w*Aw = c
+    Ax = a * x + b * w
+    Aw = b * x + c * w
+    CX, CW, CP = oracle.block_coefficients(x, w, None, Ax, Aw, None)
+    theta = 0.5 * (a + c) - np.sqrt(0.25 * (a - c) ** 2 + b * b)
+    v = np.array([b, theta - a]); v /= np.linalg.norm(v)
+    got = np.array([CX[0, 0], CW[0, 0]])
+    np.testing.assert_allclose(np.abs(got), np.abs(v), atol=1e-14)
+    assert np.sign(got[0] * got[1]) == np.sign(v[0] * v[1])
+
+
+def test_lobpcg_special_case_one_step():
+    # sbsize = k: one block step picks the k smallest Ritz pairs of span[X, W, P] (Section 5.1)
+    N, k = 5, 4
+    n = N ** 3
+    rng = _rng(8)
+    V = rng.random(n)
+    H = lambda Y: oracle.apply_H(V, N, 1.0, Y)
+    X = oracle.cholqr2(rng.standard_normal((n, k)))[0]
+    W = oracle.project(rng.standard_normal((n, k)), X)
+    Pm = oracle.project(rng.standard_normal((n, k)), X)
+    CX, CW, CP = oracle.block_coefficients(X, W, Pm, H(X), H(W), H(Pm))
+    Xn, Pn = oracle.block_update(X, W, Pm, CX, CW, CP)
+    Q = sla.orth(np.hstack([X, W, Pm]))          # SVD-based basis, independent of CholQR
+    ref = np.linalg.eigvalsh(Q.T @ H(Q))[:k]
+    Xo = oracle.cholqr2(Xn)[0]
+    got = np.linalg.eigvalsh(Xo.T @ H(Xo))
+    np.testing.assert_allclose(got, ref, rtol=1e-12)
+    np.testing.assert_allclose(Xn - X @ CX, Pn, atol=1e-13)   # step 15: X_j C_X + P_j
+
+
+def test_subblocks_split():
+    assert oracle.subblocks(10, 4) == [(0, 4), (4, 8), (8, 10)]
+    assert oracle.subblocks(8, 4) == [(0, 4), (4, 8)]
+    assert oracle.subblocks(3, 5) == [(0, 3)]
+
+
+def test_normalize_phase():
+    X = np.array([[0.1, -3.0], [-0.5, 3.0], [0.2, 1.0]])
+    Y = oracle.normalize_phase(X)
+    np.testing.assert_allclose(np.linalg.norm(Y, axis=0), 1.0)
+    assert Y[1, 0] > 0 and Y[0, 1] > 0                    # tie |-3| = |3|: lowest index wins
+
+
+# ---------------------------------------------------------------- whole solver (rows a1-a14)
+def _k_at_gap(lam_sorted, k_min):
+    """Smallest k >= k_min with lambda_k < lambda_{k+1} (does not cut a degenerate shell)."""
+    for k in range(k_min, len(lam_sorted)):
+        if lam_sorted[k] - lam_sorted[k - 1] > 1e-9:
+            return k
+    raise ValueError
+
+
+def test_ppcg_zero_potential_closed_form_spectrum():
+    N = 6
+    lam_all = np.sort([sum(4 * np.sin(np.pi * m / N) ** 2 for m in ms)
+                       for ms in itertools.product(range(N), repeat=3)])
+    k = _k_at_gap(lam_all, 7)                        # 1 + 6 = 7
+    c = 0.25                                         # constant V shifts every eigenvalue by c
+    V = np.full(N ** 3, c)
+    X0 = _rng(9).standard_normal((N ** 3, k))
+    r = oracle.ppcg(V, N, 1.0, k, 2, 5, X0, tol=1e-9)
+    assert r.converged
+    np.testing.assert_allclose(r.lam, lam_all[:k] + c, rtol=0, atol=1e-12)
+    assert np.max(r.res) <= 1e-9
+
+
+def _periodic_1d(v):
+    N = len(v)
+    T = np.diag(2.0 + v)
+    for i in range(N):
+        T[i, (i + 1) % N] -= 1.0
+        T[i, (i - 1) % N] -= 1.0
+    return T
+
+
+def test_ppcg_separable_potential_spectrum():
+    w = wl.small("sep", N=8, k=9, sbsize=3, potential="separable", seed=12)
+    rng = np.random.default_rng(w.seed)
+    v1, v2, v3 = rng.random(w.N), rng.random(w.N), rng.random(w.N)
+    V = (v1[:, None, None] + v2[None, :, None] + v3[None, None, :]).reshape(-1, order="F")
+    V_gen, X0 = wl.make_inputs(w)
+    np.testing.assert_array_equal(V, V_gen)
+    e = [np.linalg.eigvalsh(_periodic_1d(v)) for v in (v1, v2, v3)]
+    lam_all = np.sort((e[0][:, None, None] + e[1][None, :, None] + e[2][None, None, :]).ravel())
+    k = _k_at_gap(lam_all, w.k)
+    r = oracle.ppcg(V, w.N, 1.0, k, w.sbsize, 5, wl.make_inputs(w, ncols=k)[1], tol=1e-9)
+    assert r.converged
+    np.testing.assert_allclose(r.lam, lam_all[:k], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("q,rr", [(1, 5), (3, 4), (10, 5)])
+def test_ppcg_matches_dense_eigh(q, rr):
+    N, k = 7, 10
+    w = wl.small("dense", N=N, k=k, sbsize=q, seed=20 + q)
+    V, X0 = wl.make_inputs(w)
+    A = oracle.assemble_H(V, N, 1.0)
+    ev, U = np.linalg.eigh(A)
+    r = oracle.ppcg(V, N, 1.0, k, q, rr, X0, tol=1e-8)
+    assert r.converged and np.max(r.res) <= 1e-8
+    np.testing.assert_allclose(r.lam, ev[:k], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(r.X.T @ r.X, np.eye(k), atol=1e-12)
+    # Davis-Kahan: sin angle(x_i, u_i) <= r_i / gap_i
+    gaps = np.array([min(abs(ev[i] - ev[j]) for j in range(k + 1) if j != i) for i in range(k)])
+    c = np.einsum("ij,ij->j", r.X, U[:, :k])
+    sines = np.linalg.norm(r.X - U[:, :k] * c[None, :], axis=0)   # |x - (u*x) u| = sin angle
+    assert np.all(sines <= 2 * r.res / gaps + 1e-12)
+
+
+def test_ppcg_ritz_values_bound_eigenvalues_from_above():
+    # Courant-Fischer: each Ritz value from an unconverged run is >= the exact eigenvalue of the same index
+    N, k = 7, 10
+    w = wl.small("cf", N=N, k=k, sbsize=2, seed=31)
+    V, X0 = wl.make_inputs(w)
+    ev = np.linalg.eigvalsh(oracle.assemble_H(V, N, 1.0))[:k]
+    for maxiter in (0, 3, 12):
+        r = oracle.ppcg(V, N, 1.0, k, 2, 5, X0, tol=1e-8, maxiter=maxiter)
+        assert np.all(r.lam >= ev - 1e-12)
+
+
+def test_ppcg_buffer_vectors_and_no_locking():
+    N, k, nbuf = 7, 8, 3
+    w = wl.small("buf", N=N, k=k, sbsize=2, seed=41)
+    V, X0 = wl.make_inputs(w, ncols=k + nbuf)
+    ev = np.linalg.eigvalsh(oracle.assemble_H(V, N, 1.0))[:k]
+    for lock in (True, False):
+        r = oracle.ppcg(V, N, 1.0, k, 2, 5, X0, tol=1e-8, nbuf=nbuf, lock=lock)
+        assert r.converged and r.lam.shape == (k,)
+        np.testing.assert_allclose(r.lam, ev, atol=1e-10)
+
+
+def test_ppcg_projection_ablation_slows_convergence():
+    # Section 5.4, figure "proj": dropping the projections of steps 4-5 deteriorates convergence
+    N, k = 7, 10
+    w = wl.small("abl", N=N, k=k, sbsize=2, seed=51)
+    V, X0 = wl.make_inputs(w)
+    full = oracle.ppcg(V, N, 1.0, k, 2, 5, X0, tol=1e-4, maxiter=150)
+    noproj = oracle.ppcg(V, N, 1.0, k, 2, 5, X0, tol=1e-4, maxiter=150, project_W=False, project_P=False)
+    assert full.converged
+    assert (not noproj.converged) or noproj.iters > full.iters
+
+
+def test_ppcg_warm_start_converges_immediately():
+    N, k = 6, 7
+    V = np.zeros(N ** 3)
+    ev, U = np.linalg.eigh(oracle.assemble_H(V, N, 1.0))
+    r = oracle.ppcg(V, N, 1.0, k, 2, 5, np.asfortranarray(U[:, :k]), tol=1e-9)
+    assert r.converged and r.iters == 0
+
+
+# ---------------------------------------------------------------- planted mistakes are caught
+def test_planted_stencil_sign_error_is_caught():
+    real = oracle.apply_H
+
+    def bad(V, N, h, X, theta=None):                 # one neighbour enters with the wrong sign
+        return real(V, N, h, X, theta) + 2.0 * np.roll(np.asarray(X).reshape((N, N, N, -1), order="F"), 1,
+                                                       axis=0).reshape(np.asarray(X).shape, order="F")
+    N = 4
+    V = _rng().random(N ** 3)
+    X = _rng(1).standard_normal((N ** 3, 2))
+    assert not np.allclose(bad(V, N, 1.0, X), oracle.assemble_H(V, N, 1.0) @ X)
+
+
+def test_planted_missing_p_term_is_caught():
+    N, k = 5, 4
+    n = N ** 3
+    rng = _rng(8)
+    V = rng.random(n)
+    H = lambda Y: oracle.apply_H(V, N, 1.0, Y)
+    X = oracle.cholqr2(rng.standard_normal((n, k)))[0]
+    W = oracle.project(rng.standard_normal((n, k)), X)
+    Pm = oracle.project(rng.standard_normal((n, k)), X)
+    CX, CW, CP = oracle.block_coefficients(X, W, Pm, H(X), H(W), H(Pm))
+    Xbad = X @ CX + W @ CW                           # step 14 without the P_j C_P term
+    Q = sla.orth(np.hstack([X, W, Pm]))
+    ref = np.linalg.eigvalsh(Q.T @ H(Q))[:k]
+    got = np.linalg.eigvalsh(oracle.cholqr2(Xbad)[0].T @ H(oracle.cholqr2(Xbad)[0]))
+    assert not np.allclose(got, ref, rtol=1e-8)
+
+
+def test_planted_transposed_projection_is_caught():
+    rng = _rng(4)
+    X = oracle.cholqr2(rng.standard_normal((200, 7)))[0]
+    Y = rng.standard_normal((200, 7))
+    bad = Y - X @ (Y.T @ X)                            # transposed Gram
+    assert np.max(np.abs(X.T @ bad)) > 1e-3
