@@ -1,0 +1,103 @@
+// Internal declarations shared by the CUDA translation units of the PPCG library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace ppcg {
+
+// ---------------------------------------------------------------------------------------------- constants
+// Numerical thresholds of the method (shared by every kernel that takes the decision).
+constexpr double kPivotTol = 1e-7;      // sub-block problems: smallest Cholesky diagonal of unit-diagonal S*S
+constexpr double kAlphaTol = 1e-12;     // Theorem 1: smallest singular value of C_X
+constexpr double kCholPivotTol = 1e-7;  // CholQR: smallest relative pivot R_ii / sqrt(G_ii)
+constexpr double kJacobiTol = 1e-16;    // Jacobi: rotate while |a_pq| > kJacobiTol * ||A||_F
+constexpr int kJacobiMaxSweeps = 60;
+constexpr int kMaxSbsize = 16;          // 3q <= 48 fits the warp-level sub-block solver
+
+// Error-flag bits written by kernels into the handle's device flag word.
+enum : int { kFlagCholBreakdown = 1, kFlagTimeout = 2, kFlagJacobiNoConv = 4 };
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Process-wide count of kernels launched by this library (reported per solve in ppcg_stats).
+void count_launch(int n = 1);
+long long launch_count();
+
+// ---------------------------------------------------------------------------------------------- operator
+struct Grid {
+  int nx, ny, nz;
+  double inv_h2;
+};
+
+// Y[:, c] = A X[:, c] for c < m; dg = 6/h^2 + V (n doubles).
+cudaError_t stencil_apply(const Grid& g, const double* dg, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                          int m, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------------- FP64 GEMMs
+// Number of doubles of split-K partial storage used by gram() for these sizes.
+int gram_splits(int64_t n, int ma, int mb, size_t part_capacity);
+// C (ma x mb, ldc) = A^T B, reduction over n rows; symmetric = (A == B, ma == mb): only upper tiles computed
+// and mirrored so that C is exactly symmetric.
+cudaError_t gram(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n, int ma, int mb, double* C,
+                 int ldc, bool symmetric, double* part, size_t part_capacity, cudaStream_t s);
+
+enum class Epi : int { Store = 0, Sub = 1, Residual = 2 };
+struct ResidualArgs {
+  const double* dg;     // 6/h^2 + V
+  double sigma;         // preconditioner shift
+  double delta;         // preconditioner floor
+  double* norm_part;    // [row tiles][p] partial column norms^2
+};
+// Store:    Y = A G
+// Sub:      Y = Y - A G                       (in place)
+// Residual: R = Yin - A G; Y = T R; norm_part = per-tile column sums of R^2
+// A: n x m (lda), G: m x p (ldg), Y: n x p (ldy). g_upper: G is upper triangular (K loop trimmed).
+cudaError_t gemm_nn(const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p, double* Y,
+                    int64_t ldy, const double* Yin, int64_t ldyin, Epi epi, bool g_upper, const ResidualArgs* ra,
+                    cudaStream_t s);
+int64_t norm_row_tiles(int64_t n);   // row tiles of gemm_nn / residual_diag (norm_part has this many rows)
+
+// ---------------------------------------------------------------------------------------------- vectors
+// R = HX - X diag(lam); W = T R; norm_part per row tile.
+cudaError_t residual_diag(const double* X, const double* HX, int64_t ld, int64_t n, int m, const double* lam,
+                          const ResidualArgs& ra, double* W, cudaStream_t s);
+// out[c] = sum over row tiles of norm_part[t * m + c]
+cudaError_t reduce_colnorms(const double* norm_part, int64_t tiles, int m, double* out, cudaStream_t s);
+// out[:, j] = idx[j] >= 0 ? in[:, idx[j]] : 0 for j < m
+cudaError_t gather_cols(const double* in, int64_t ldi, double* out, int64_t ldo, int64_t n, const int* idx, int m,
+                        cudaStream_t s);
+// Unit norm and largest-modulus entry (lowest index on ties) positive, in place on n x m.
+cudaError_t normalize_phase(double* X, int64_t ld, int64_t n, int m, double* scratch, cudaStream_t s);
+// dg = 6 * inv_h2 + V
+cudaError_t make_diag(const double* V, double inv_h2, int64_t n, double* dg, cudaStream_t s);
+// count non-finite entries of v[0..m) into *bad (device int)
+cudaError_t check_finite(const double* v, int m, int* bad, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------------- sub-blocks
+struct BlockArgs {
+  const double *X, *W, *P, *HX, *HW, *HP;
+  int64_t ld, n;
+  int k_act, q, has_p;
+};
+size_t block_gram_part_elems(int64_t n, int k_act, int q);
+cudaError_t block_gram(const BlockArgs& a, double* part, size_t part_capacity, int* nchunk_out, cudaStream_t s);
+cudaError_t block_solve(const BlockArgs& a, const double* part, int nchunk, double* coef, int* flags,
+                        int* counters, cudaStream_t s);
+cudaError_t block_update(double* X, const double* W, double* P, int64_t ld, int64_t n, int k_act, int q,
+                         int has_p, const double* coef, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------------- dense k x k
+size_t chol_ws_elems(int m);
+// Rinv (m x m, ldr = m, upper) = R^{-1} for G + shift I = R^T R (G m x m, ldg = m). Sets kFlagCholBreakdown in
+// *flag on a relative pivot below kCholPivotTol.
+cudaError_t chol_inv(const double* G, int m, double shift, double* Rinv, double* ws, int* flag, unsigned* bar,
+                     cudaStream_t s);
+size_t jacobi_ws_elems(int m);
+// lambda ascending (m), C (m x m) eigenvectors of symmetric M (m x m, upper read).
+cudaError_t jacobi_eigh(const double* M, int m, double* lambda, double* C, double* ws, int* flag, unsigned* bar,
+                        int* sweeps_out_dev, cudaStream_t s);
+size_t barrier_words();
+
+}  // namespace ppcg

@@ -1,0 +1,157 @@
+// Column-wise kernels of Algorithm 3: the Ritz residual with the preconditioner fused (steps 25 and 8), column
+// norms, column gathers for locking/compaction (steps 27-29), the output phase convention, and small helpers.
+// All are HBM-bound streaming kernels (one read and at most one write per element).
+#include "ppcg_internal.h"
+
+namespace ppcg {
+
+namespace {
+
+constexpr int kRows = 64;   // rows per tile; must match gemm_nn's row tile (norm_part layout)
+
+// R = HX - lam_c X; W = R / max(dg - sigma, delta); per-tile sums of R^2 per column.
+__global__ void __launch_bounds__(256)
+residual_diag_kernel(const double* __restrict__ X, const double* __restrict__ HX, int64_t ld, int64_t n, int m,
+                     const double* __restrict__ lam, const double* __restrict__ dg, double sigma, double delta,
+                     double* __restrict__ W, double* __restrict__ norm_part) {
+  const int r_loc = threadIdx.x % kRows;
+  const int c_loc = threadIdx.x / kRows;          // 4 columns per block
+  const int64_t r = (int64_t)blockIdx.x * kRows + r_loc;
+  const int c = blockIdx.y * 4 + c_loc;
+  double sq = 0.0;
+  if (r < n && c < m) {
+    const int64_t o = (int64_t)c * ld + r;
+    const double rr = HX[o] - lam[c] * X[o];
+    sq = rr * rr;
+    W[o] = rr / fmax(dg[r] - sigma, delta);
+  }
+  // reduce over the 64 rows of this column: two warps
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
+  __shared__ double red[8];
+  const int warp = threadIdx.x / 32;
+  if ((threadIdx.x & 31) == 0) red[warp] = sq;
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    const int cc = blockIdx.y * 4 + threadIdx.x;
+    if (cc < m) norm_part[(int64_t)blockIdx.x * m + cc] = red[2 * threadIdx.x] + red[2 * threadIdx.x + 1];
+  }
+}
+
+__global__ void reduce_colnorms_kernel(const double* __restrict__ part, int64_t tiles, int m, double* out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m) return;
+  double s = 0.0;
+  for (int64_t t = 0; t < tiles; ++t) s += part[t * m + c];
+  out[c] = s;
+}
+
+__global__ void gather_cols_kernel(const double* __restrict__ in, int64_t ldi, double* __restrict__ out, int64_t ldo,
+                                   int64_t n, const int* __restrict__ idx) {
+  const int j = blockIdx.y;
+  const int src = idx[j];
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    out[(int64_t)j * ldo + r] = (src >= 0) ? in[(int64_t)src * ldi + r] : 0.0;
+}
+
+// One block per column: norm^2 and the (first) index of the largest |x|; then scale by sign(x_p)/norm.
+__global__ void __launch_bounds__(1024) phase_kernel(double* X, int64_t ld, int64_t n) {
+  double* x = X + (int64_t)blockIdx.x * ld;
+  double sq = 0.0, best = -1.0;
+  int64_t bi = 0;
+  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+    const double v = x[r];
+    sq += v * v;
+    const double a = fabs(v);
+    if (a > best) { best = a; bi = r; }   // rows visited ascending: keeps the first maximum
+  }
+  __shared__ double s_sq[32], s_best[32];
+  __shared__ long long s_bi[32];
+  for (int off = 16; off > 0; off >>= 1) {
+    sq += __shfl_down_sync(0xffffffffu, sq, off);
+    const double ob = __shfl_down_sync(0xffffffffu, best, off);
+    const long long oi = __shfl_down_sync(0xffffffffu, (long long)bi, off);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  if (lane == 0) { s_sq[warp] = sq; s_best[warp] = best; s_bi[warp] = bi; }
+  __syncthreads();
+  __shared__ double scale;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) / 32;
+    double t = 0.0, b = -1.0;
+    long long i = 0;
+    for (int w = 0; w < nw; ++w) {
+      t += s_sq[w];
+      if (s_best[w] > b || (s_best[w] == b && s_bi[w] < i)) { b = s_best[w]; i = s_bi[w]; }
+    }
+    const double sgn = (x[i] < 0.0) ? -1.0 : 1.0;
+    scale = sgn / sqrt(t);
+  }
+  __syncthreads();
+  const double sc = scale;
+  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) x[r] *= sc;
+}
+
+__global__ void make_diag_kernel(const double* __restrict__ V, double six_inv_h2, int64_t n, double* dg) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    dg[r] = six_inv_h2 + V[r];
+}
+
+__global__ void check_finite_kernel(const double* __restrict__ v, int m, int* bad) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    if (!isfinite(v[i])) atomicAdd(bad, 1);
+}
+
+}  // namespace
+
+int64_t norm_row_tiles(int64_t n) { return ceil_div(n, kRows); }
+
+cudaError_t residual_diag(const double* X, const double* HX, int64_t ld, int64_t n, int m, const double* lam,
+                          const ResidualArgs& ra, double* W, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  dim3 grid((unsigned)norm_row_tiles(n), (unsigned)ceil_div(m, 4));
+  residual_diag_kernel<<<grid, 256, 0, s>>>(X, HX, ld, n, m, lam, ra.dg, ra.sigma, ra.delta, W, ra.norm_part);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t reduce_colnorms(const double* norm_part, int64_t tiles, int m, double* out, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  reduce_colnorms_kernel<<<(unsigned)ceil_div(m, 128), 128, 0, s>>>(norm_part, tiles, m, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t gather_cols(const double* in, int64_t ldi, double* out, int64_t ldo, int64_t n, const int* idx, int m,
+                        cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  const int64_t bx = ceil_div(n, 256);
+  dim3 grid((unsigned)(bx < 1024 ? bx : 1024), m);
+  gather_cols_kernel<<<grid, 256, 0, s>>>(in, ldi, out, ldo, n, idx);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t normalize_phase(double* X, int64_t ld, int64_t n, int m, double* /*scratch*/, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  phase_kernel<<<m, 1024, 0, s>>>(X, ld, n);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t make_diag(const double* V, double inv_h2, int64_t n, double* dg, cudaStream_t s) {
+  make_diag_kernel<<<(unsigned)(ceil_div(n, 256) < 4096 ? ceil_div(n, 256) : 4096), 256, 0, s>>>(V, 6.0 * inv_h2, n,
+                                                                                                  dg);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t check_finite(const double* v, int m, int* bad, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  check_finite_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(v, m, bad);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace ppcg

@@ -1,0 +1,212 @@
+"""GPU PPCG (Algorithm 3) through the C ABI against the CPU oracle, dense eigh and stored oracle values.
+
+Bars: eigenvalues |lambda_gpu - lambda_ref| / max(|lambda_ref|, 1) <= 1e-10 (FP64 form); every returned pair
+has ||A x - lambda x|| <= tol (recomputed on the CPU with the oracle's operator); X^T X = I to 1e-12;
+eigenvectors within the Davis-Kahan bound sin(angle) <= (r_gpu + r_ref) / gap.
+"""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from tests.gpu_helpers import need_gpu, torch  # noqa: F401
+import paper_1407_7506_gb300 as pk
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+LAM_TOL = 1e-10
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def _gpu_solve(V, N, k, q, rr, X0, tol=1e-8, nbuf=0, lock=True, maxiter=3000, history=0):
+    s = pk.Solver(V, N, k, q, rr_period=rr, nbuf=nbuf, lock=lock, maxiter=maxiter, history=history)
+    try:
+        lam, X, res, st = s.solve(X0, tol)
+        return lam, X.cpu().numpy().T.copy(), res, st
+    finally:
+        s.close()
+
+
+def _check_pairs(V, N, lam, X, tol):
+    res = np.linalg.norm(oracle.apply_H(V, N, 1.0, X) - X * lam[None, :], axis=0)
+    assert np.max(res) <= tol * (1 + 1e-6), np.max(res)
+    np.testing.assert_allclose(X.T @ X, np.eye(X.shape[1]), atol=1e-12)
+    assert np.all(np.diff(lam) >= -1e-14)
+    for i in range(X.shape[1]):               # phase convention
+        p = int(np.argmax(np.abs(X[:, i])))
+        assert X[p, i] > 0
+    return res
+
+
+def _rel(a, b):
+    return np.abs(a - b) / np.maximum(np.abs(b), 1.0)
+
+
+@pytest.mark.parametrize("N,k,q,rr,nbuf,lock", [
+    (8, 8, 2, 5, 0, True),
+    (8, 10, 1, 5, 0, True),
+    (9, 12, 3, 4, 2, True),
+    (8, 9, 4, 5, 0, False),
+    (8, 12, 12, 5, 0, True),       # sbsize = k: the LOBPCG special case of Section 5.1
+    (10, 20, 6, 5, 0, True),       # last sub-block 2 columns
+])
+def test_solve_matches_oracle_and_dense(N, k, q, rr, nbuf, lock):
+    w = wl.small("p", N=N, k=k, sbsize=q, seed=60 + N + k + q)
+    V, X0 = wl.make_inputs(w, ncols=k + nbuf)
+    lam, X, res, st = _gpu_solve(V, N, k, q, rr, X0, nbuf=nbuf, lock=lock)
+    assert st["status"] == "ok" and st["converged"] == 1
+    _check_pairs(V, N, lam, X, 1e-8)
+    np.testing.assert_allclose(res, np.linalg.norm(oracle.apply_H(V, N, 1.0, X) - X * lam, axis=0), rtol=1e-3,
+                               atol=1e-13)
+    ev, U = np.linalg.eigh(oracle.assemble_H(V, N, 1.0))
+    assert np.all(_rel(lam, ev[:k]) <= LAM_TOL)
+    ref = oracle.ppcg(V, N, 1.0, k, q, rr, X0, tol=1e-8, nbuf=nbuf, lock=lock, maxiter=3000)
+    assert ref.converged
+    assert np.all(_rel(lam, ref.lam) <= LAM_TOL)
+    # iteration counts are not pinned (rounding differences grow chaotically), but must be alike
+    assert st["iters"] <= 2 * ref.iters + 50, (st["iters"], ref.iters)
+    # Davis-Kahan against the oracle's vectors
+    gaps = np.array([np.min(np.abs(np.delete(ev[:k + 1], i) - ev[i])) for i in range(k)])
+    for i in range(k):
+        c = X[:, i] @ ref.X[:, i]
+        sin = np.linalg.norm(X[:, i] - c * ref.X[:, i])
+        assert sin <= (res[i] + ref.res[i]) / gaps[i] + 1e-10
+
+
+def _oracle_history(ref):
+    out = []
+    for h in ref.history:
+        if h["rr"]:
+            out.append((h["iter"], 1, h["max_res"], h["trace"]))
+        else:
+            out.append((h["iter"], 0, h["w_fro"], 0.0))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("N,k,q", [(8, 10, 2), (9, 12, 4)])
+def test_iteration_history_tracks_oracle(N, k, q):
+    # the same iteration from the same start: ||W||_F after each plain step and the Ritz residual / trace at
+    # each Rayleigh-Ritz step agree with the oracle while rounding differences are still small
+    w = wl.small("hist", N=N, k=k, sbsize=q, seed=90 + N)
+    V, X0 = wl.make_inputs(w)
+    lam, X, res, st = _gpu_solve(V, N, k, q, 5, X0, history=4000)
+    ref = oracle.ppcg(V, N, 1.0, k, q, 5, X0, tol=1e-8, maxiter=3000)
+    g, o = st["history"], _oracle_history(ref)
+    early = min(len(g), len(o), 12)
+    np.testing.assert_array_equal(g[:early, :2], o[:early, :2])
+    rel = np.abs(g[:early, 2] - o[:early, 2]) / np.abs(o[:early, 2])
+    assert np.all(rel[g[:early, 0] <= 5] <= 1e-8), rel
+    assert np.all(rel <= 1e-4), rel
+    tr = g[:early, 1] == 1
+    np.testing.assert_allclose(g[:early][tr, 3], o[:early][tr, 3], rtol=1e-12)
+
+
+def test_solve_k1():
+    N, k = 6, 1
+    V, X0 = wl.make_inputs(wl.small("k1", N=N, k=k, sbsize=1, seed=3))
+    lam, X, res, st = _gpu_solve(V, N, k, 1, 5, X0)
+    assert st["converged"] == 1
+    ev = np.linalg.eigvalsh(oracle.assemble_H(V, N, 1.0))
+    assert _rel(lam, ev[:1])[0] <= LAM_TOL
+    _check_pairs(V, N, lam, X, 1e-8)
+
+
+def test_solve_config1_against_dense_golden():
+    # 16^3 grid, k = 64, sbsize = 1, rr_period = 5, V ~ U[0, 1)
+    w = wl.CONFIGS[1]
+    V, X0 = wl.make_inputs(w)
+    gold = np.loadtxt(os.path.join(GOLDEN, "config1_dense_eigs.txt"))[:w.k]
+    lam, X, res, st = _gpu_solve(V, w.N, w.k, w.sbsize, w.rr_period, X0, tol=w.tol, maxiter=5000)
+    assert st["converged"] == 1, st
+    assert np.all(_rel(lam, gold) <= LAM_TOL), np.max(_rel(lam, gold))
+    _check_pairs(V, w.N, lam, X, w.tol)
+
+
+def test_solve_config2_full_size():
+    # 32^3 grid, k = 256, sbsize = 4, 8 Gaussian wells: the benchmarked workload
+    w = wl.CONFIGS[2]
+    V, X0 = wl.make_inputs(w)
+    lam, X, res, st = _gpu_solve(V, w.N, w.k, w.sbsize, w.rr_period, X0, tol=w.tol, maxiter=5000)
+    assert st["converged"] == 1, st
+    np.testing.assert_allclose(X.T @ X, np.eye(w.k), atol=1e-12)
+    cols = np.random.default_rng(0).choice(w.k, 24, replace=False)
+    r = np.linalg.norm(oracle.apply_H(V, w.N, 1.0, X[:, cols]) - X[:, cols] * lam[cols], axis=0)
+    assert np.max(r) <= w.tol * (1 + 1e-6)
+    path = os.path.join(GOLDEN, "config2_oracle_eigs.txt")
+    if os.path.exists(path):
+        gold = np.loadtxt(path)[:, 0]
+        assert np.all(_rel(lam, gold) <= LAM_TOL), np.max(_rel(lam, gold))
+
+
+# ------------------------------------------------------------------------------------- edge cases
+def test_maxiter_one_returns_last_ritz_pairs():
+    N, k = 7, 6
+    V, X0 = wl.make_inputs(wl.small("m1", N=N, k=k, sbsize=2, seed=4))
+    ev = np.linalg.eigvalsh(oracle.assemble_H(V, N, 1.0))[:k]
+    lam1, X1, res1, st1 = _gpu_solve(V, N, k, 2, 5, X0, maxiter=1)
+    assert st1["status"] == "not_converged" and st1["iters"] == 1 and st1["converged"] == 0
+    assert np.all(lam1 >= ev - 1e-12)          # Courant-Fischer: Ritz values bound from above
+    np.testing.assert_allclose(X1.T @ X1, np.eye(k), atol=1e-12)
+
+
+def test_warm_start_converges_at_iteration_zero():
+    N, k = 6, 7
+    V = np.zeros(N ** 3)
+    ev, U = np.linalg.eigh(oracle.assemble_H(V, N, 1.0))
+    lam, X, res, st = _gpu_solve(V, N, k, 2, 5, np.asfortranarray(U[:, :k]))
+    assert st["converged"] == 1 and st["iters"] == 0
+    np.testing.assert_allclose(lam, ev[:k], atol=1e-12)
+
+
+def test_rank_deficient_start_uses_cholqr_fallback():
+    N, k = 7, 6
+    V, X0 = wl.make_inputs(wl.small("rd", N=N, k=k, sbsize=2, seed=5))
+    X0 = np.array(X0)
+    X0[:, 3] = X0[:, 1]
+    lam, X, res, st = _gpu_solve(V, N, k, 2, 5, np.asfortranarray(X0))
+    assert st["n_cholqr_fallback"] >= 1 and st["converged"] == 1
+    ev = np.linalg.eigvalsh(oracle.assemble_H(V, N, 1.0))[:k]
+    assert np.all(_rel(lam, ev) <= LAM_TOL)
+
+
+def test_nan_potential_reports_numeric_error():
+    N, k = 6, 4
+    V, X0 = wl.make_inputs(wl.small("nan", N=N, k=k, sbsize=2, seed=6))
+    V = V.copy()
+    V[10] = np.nan
+    with pytest.raises(pk.PPCGError) as e:
+        _gpu_solve(V, N, k, 2, 5, X0)
+    assert e.value.status == pk.PPCG_ERR_NUMERIC
+
+
+def test_host_buffers_through_the_c_abi():
+    # X0, X, lambda and resnorm in host memory: the library copies across itself
+    N, k, q = 8, 6, 2
+    V, X0 = wl.make_inputs(wl.small("host", N=N, k=k, sbsize=q, seed=8))
+    n = N ** 3
+    op = pk.ppcg_operator(N, N, N, 1.0, V.ctypes.data, (ctypes.c_double * 3)(0, 0, 0), 0)
+    h = pk.ppcg_create(op, n, k, q, 5)
+    try:
+        X0c = np.asfortranarray(X0)
+        X = np.zeros((n, k), order="F")
+        lam, res = np.zeros(k), np.zeros(k)
+        st = pk.ppcg_stats()
+        assert pk.ppcg_solve(h, X0c.ctypes.data, 1e-8, lam.ctypes.data, X.ctypes.data, res.ctypes.data, st) == 0
+        ev = np.linalg.eigvalsh(oracle.assemble_H(V, N, 1.0))[:k]
+        assert np.all(_rel(lam, ev) <= LAM_TOL)
+        _check_pairs(V, N, lam, X, 1e-8)
+        # set_potential: a constant shift moves every eigenvalue by the same amount
+        Vs = np.ascontiguousarray(V + 0.5)            # kept alive across the call
+        pk.ppcg_set_potential(h, Vs.ctypes.data)
+        lam2 = np.zeros(k)
+        assert pk.ppcg_solve(h, X0c.ctypes.data, 1e-8, lam2.ctypes.data, X.ctypes.data, None, None) == 0
+        np.testing.assert_allclose(lam2, lam + 0.5, atol=1e-10)
+    finally:
+        pk.ppcg_destroy(h)
