@@ -87,7 +87,7 @@ typedef struct {
   int32_t n_early_rr;         /* Rayleigh-Ritz steps forced by ||W||_F <= tol */
   int32_t converged;          /* 1 if max residual <= tol */
   int32_t history_len;        /* entries written to options.history */
-  int32_t pad0;
+  int32_t jacobi_sweeps_max;  /* most Jacobi sweeps one Rayleigh-Ritz eigensolve needed */
   int64_t kernel_launches;    /* device kernels this solve launched */
   double t_phase_ms[8];       /* per-phase device time (ms) when options.timing = 1 */
   double max_res;             /* max_i ||A x_i - lambda_i x_i|| over the k returned pairs */

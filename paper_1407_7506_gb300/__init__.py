@@ -45,11 +45,11 @@ class ppcg_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("n_rr", ctypes.c_int32), ("n_locked", ctypes.c_int32),
                 ("n_drop_p", ctypes.c_int32), ("n_stall", ctypes.c_int32), ("n_cholqr_fallback", ctypes.c_int32),
                 ("n_early_rr", ctypes.c_int32), ("converged", ctypes.c_int32), ("history_len", ctypes.c_int32),
-                ("pad0", ctypes.c_int32), ("kernel_launches", ctypes.c_int64), ("t_phase_ms", ctypes.c_double * 8),
+                ("jacobi_sweeps_max", ctypes.c_int32), ("kernel_launches", ctypes.c_int64), ("t_phase_ms", ctypes.c_double * 8),
                 ("max_res", ctypes.c_double)]
 
     def as_dict(self):
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("t_phase_ms", "pad0")}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "t_phase_ms"}
         d["t_phase_ms"] = dict(zip(PHASES, list(self.t_phase_ms)))
         return d
 

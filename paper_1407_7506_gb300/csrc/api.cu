@@ -52,6 +52,7 @@ struct ppcg_ctx {
   std::vector<int> evphase;
   size_t evused = 0;
   double t_ms[8] = {};
+  int last_sweeps = 0;
 };
 
 namespace {
@@ -273,6 +274,14 @@ ppcg_status dense_eigh(ppcg_ctx* c, const double* Mm, int m, double* lam, double
   return PPCG_OK;
 }
 
+// sweeps used by the last dense_eigh (synchronises)
+int last_sweeps(ppcg_ctx* c) {
+  int info[2] = {0, 0};
+  if (cudaMemcpyAsync(info, c->jinfo, sizeof(info), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) return -1;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return -1;
+  return info[0];
+}
+
 ResidualArgs resid_args(ppcg_ctx* c, double sigma) {
   ResidualArgs ra{};
   ra.dg = c->dg;
@@ -322,6 +331,10 @@ ppcg_status rr_step(ppcg_ctx* c, SolveState& st, bool allow_compact, ppcg_stats*
   CK(cudaMemcpy(&fl, c->iflag, sizeof(int), cudaMemcpyDeviceToHost));
   if (fl & kFlagTimeout) return PPCG_ERR_TIMEOUT;
   st.sigma = c->lam_h[0];
+  if (stats) {
+    const int sw = last_sweeps(c);
+    if (sw > stats->jacobi_sweeps_max) stats->jacobi_sweeps_max = sw;
+  }
   ResidualArgs ra = resid_args(c, st.sigma);
   CK(residual_diag(c->X, c->HX, c->ld, c->n, kt, c->lam, ra, c->W, c->stream));
   CK(reduce_colnorms(c->normpart, norm_row_tiles(c->n), kt, c->norms, c->stream));
@@ -680,6 +693,7 @@ ppcg_status ppcg_cholqr2(ppcg_handle c, double* X, int64_t ldx, int32_t m, int32
 ppcg_status ppcg_dense_eigh(ppcg_handle c, const double* M, int32_t m, double* lambda, double* C) {
   if (!c || !M || !lambda || !C || m < 1 || m > c->kt) return PPCG_ERR_ARG;
   PS(dense_eigh(c, M, m, lambda, C));
+  c->last_sweeps = last_sweeps(c);
   const int f = read_flag(c);
   if (f < 0) return PPCG_ERR_CUDA;
   if (f & kFlagTimeout) return PPCG_ERR_TIMEOUT;

@@ -163,7 +163,7 @@ __device__ void warp_jacobi(double* K, double* Z, int m, int mp, int ld, double*
     nrm += v * v;
   }
   for (int off = 16; off > 0; off >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, off);
-  const double thr = kJacobiTol * sqrt(nrm);
+  const double thr = kJacobiTolSmall * sqrt(nrm);
   __syncwarp();
   const int P = mp / 2;
   for (int sweep = 0; sweep < kJacobiMaxSweeps; ++sweep) {

@@ -12,7 +12,9 @@ namespace ppcg {
 constexpr double kPivotTol = 1e-7;      // sub-block problems: smallest Cholesky diagonal of unit-diagonal S*S
 constexpr double kAlphaTol = 1e-12;     // Theorem 1: smallest singular value of C_X
 constexpr double kCholPivotTol = 1e-7;  // CholQR: smallest relative pivot R_ii / sqrt(G_ii)
-constexpr double kJacobiTol = 1e-16;    // Jacobi: rotate while |a_pq| > kJacobiTol * ||A||_F
+constexpr double kJacobiTol = 1e-14;    // k x k Jacobi: rotate while |a_pq| > kJacobiTol * ||A||_F; an off-diagonal
+                                        // left below that adds < ~1e-12 to a Ritz residual (tol is 1e-8)
+constexpr double kJacobiTolSmall = 1e-16;  // sub-block warp Jacobi
 constexpr int kJacobiMaxSweeps = 60;
 constexpr int kMaxSbsize = 16;          // 3q <= 48 fits the warp-level sub-block solver
 
