@@ -63,6 +63,19 @@ PPCG_API ppcg_status ppcg_block_update(ppcg_handle h, double* X, const double* W
 PPCG_API ppcg_status ppcg_residual(ppcg_handle h, const double* X, const double* HX, int64_t ld, int32_t m, const double* M,
                           const double* lam, double sigma, double* W, double* colnorm2);
 
+/* Gram matrix C = A^T B without a handle and without allocating any device memory. The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate (a fixed device-memory budget, an
+ * application memory pool that forbids cudaMalloc, no ppcg handle). A is n x ma (lda >= n), B is n x mb
+ * (ldb >= n), C is ma x mb with leading dimension ma; all device pointers. Runs on cuda_stream (NULL = legacy
+ * default stream) and returns without synchronising.
+ * Limit: ma * mb <= 1,048,576 (the partial sums use a static 8 MiB device array that every GPU loading this
+ * library holds until the process exits); larger sizes return PPCG_ERR_ARG and enqueue nothing.
+ * The first call on a device looks the array's device address up (cudaGetSymbolAddress), so make that first
+ * call before any stream capture. All calls share the one array and nothing in it needs to start at zero, but
+ * calls that overlap on the GPU (other streams, other threads) race on it: serialise them. */
+PPCG_API ppcg_status ppcg_gram_noalloc(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n,
+                                       int32_t ma, int32_t mb, double* C, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,7 @@ PHASES = ("AX", "GEMM", "BlockRR", "CholQR", "RR", "Precond", "Lock", "Other")
 
 EXPORTS = ("ppcg_status_string", "ppcg_workspace_bytes", "ppcg_create", "ppcg_set_potential", "ppcg_solve",
            "ppcg_destroy", "ppcg_apply_operator", "ppcg_gram", "ppcg_project", "ppcg_cholqr2", "ppcg_dense_eigh",
-           "ppcg_block_coefficients", "ppcg_block_update", "ppcg_residual")
+           "ppcg_block_coefficients", "ppcg_block_update", "ppcg_residual", "ppcg_gram_noalloc")
 
 
 class ppcg_operator(ctypes.Structure):
@@ -88,6 +88,7 @@ def lib():
             "ppcg_block_coefficients": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i64, _i32, _i32, _vp, _vp]),
             "ppcg_block_update": (_i32, [_vp, _vp, _vp, _vp, _i64, _i32, _i32, _vp]),
             "ppcg_residual": (_i32, [_vp, _vp, _vp, _i64, _i32, _vp, _vp, _d, _vp, _vp]),
+            "ppcg_gram_noalloc": (_i32, [_vp, _i64, _vp, _i64, _i64, _i32, _i32, _vp, _vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -170,6 +171,11 @@ def ppcg_block_update(h, X, W, P, ld, k_act, has_p, coef):
 
 def ppcg_residual(h, X, HX, ld, m, M, lam, sigma, W, colnorm2):
     _check(lib().ppcg_residual(h, X, HX, ld, m, M, lam, sigma, W, colnorm2), "ppcg_residual")
+
+
+def ppcg_gram_noalloc(A, lda, B, ldb, n, ma, mb, C, stream=0):
+    """C = A^T B without a handle and without device allocation (static scratch; ma * mb <= 2**20)."""
+    _check(lib().ppcg_gram_noalloc(A, lda, B, ldb, n, ma, mb, C, stream), "ppcg_gram_noalloc")
 
 
 from .solver import Solver  # noqa: E402,F401

@@ -12,6 +12,9 @@
 // keep the FP64 pipe fed: 64 x 64 output tiles, 16-deep K slices staged in shared memory, 4 x 4 register
 // micro-tiles per thread (16 DFMA per 2 vector shared loads).
 #include "ppcg_internal.h"
+#include "ppcg_steps.h"
+
+#include <mutex>
 
 namespace ppcg {
 
@@ -232,3 +235,44 @@ cudaError_t gemm_nn(const double* A, int64_t lda, const double* G, int ldg, int6
 }
 
 }  // namespace ppcg
+
+// ------------------------------------------------------------------------------------------ allocation-free Gram
+// ppcg_gram_noalloc serves callers that cannot allocate device memory at all: code that runs under a fixed,
+// pre-reserved memory budget or inside an application's own memory pool that forbids cudaMalloc (whose implicit
+// synchronisation such callers also cannot afford), and callers that have no ppcg handle (creating one allocates a
+// workspace). Its split-K partial sums live in the file-scope array below instead of a caller-provided or
+// library-allocated workspace. Every GPU that loads this library holds the array until the process exits.
+namespace {
+constexpr size_t kNoAllocScratchDoubles = size_t(1) << 20;   // 8 MiB: ma * mb must not exceed 1,048,576
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_addr[kMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) double g_gram_scratch[kNoAllocScratchDoubles];
+
+extern "C" ppcg_status ppcg_gram_noalloc(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n,
+                                         int32_t ma, int32_t mb, double* C, void* cuda_stream) {
+  if (!A || !B || !C || n < 1 || ma < 1 || mb < 1 || lda < n || ldb < n) return PPCG_ERR_ARG;
+  if ((size_t)ma * (size_t)mb > kNoAllocScratchDoubles) return PPCG_ERR_ARG;   // beyond the static scratch
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PPCG_ERR_CUDA;
+  double* scratch = nullptr;
+  {
+    // Set-up, once per device, with that device current: the array's name is only a host-side stand-in, so
+    // the device address must come from the runtime.
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_gram_scratch) != cudaSuccess || !p) return PPCG_ERR_CUDA;
+      g_noalloc_addr[dev] = static_cast<double*>(p);
+    }
+    scratch = g_noalloc_addr[dev];
+  }
+  const bool sym = (A == B && lda == ldb && ma == mb);
+  if (ppcg::gram(A, lda, B, ldb, n, ma, mb, C, ma, sym, scratch, kNoAllocScratchDoubles,
+                 static_cast<cudaStream_t>(cuda_stream)) != cudaSuccess)
+    return PPCG_ERR_CUDA;
+  return PPCG_OK;
+}
+
