@@ -35,8 +35,9 @@ import workloads as wl  # noqa: E402
 METRIC = "time-to-tol 1e-8 and PPCG iters/s, mixed vs FP64 form on 1 GB300; % roofline"
 # FP64 FMA pipe of GB300: 2 FMA lanes per SM per clock (measured: a DFMA stream reaches 1.195 TFLOP/s at 1.97 GHz)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12          # 1.2586, at the 2070 MHz maximum SM clock
-# dram bytes (read + write) per launch of the roofline kernel from one ncu capture of this shape, or None
-ROOFLINE_TRAFFIC_BYTES = None
+# dram bytes (read + write) per launch of the roofline kernel, from one ncu capture of this shape
+# (profiles/gram_tn_kernel_grid32_k256.md: 134.66 MB read + 9.42 MB written)
+ROOFLINE_TRAFFIC_BYTES = 144.08e6
 L2_BYTES = 129 * 2 ** 20
 
 
@@ -186,6 +187,7 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=3, help="oracle iterations in the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     args = ap.parse_args()
     w = wl.CONFIGS[int(args.workload)]
     if args.impl == "reference":
@@ -210,60 +212,68 @@ def main():
     V, X0 = wl.make_inputs(w)
     V_d = torch.from_numpy(V).to(dev)
     X0_d = torch.from_numpy(np.ascontiguousarray(X0.T)).to(dev)         # (k, n) rows = columns of X0
-    solver = pk.Solver(V_d, w.N, w.k, w.sbsize, rr_period=w.rr_period, maxiter=args.maxiter, device=dev,
-                       stream=stream)
-    X_out = torch.empty((w.k, w.n), dtype=torch.float64, device=dev)
-
-    def step():
-        lam, _, res, st = solver.solve(X0_d, w.tol, out=X_out)
-        return lam, res, st
-
-    for _ in range(args.warmup):
-        lam, res, st = step()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    iters, launches, stats = 0, 0, []
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        ev0.record(stream)
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            lam, res, st = step()
-            iters += st["iters"]
-            launches += st["kernel_launches"]
-            stats.append(st)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-    if dist:
-        dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    ms_per_step = ms / args.steps
-    converged = all(s["converged"] == 1 for s in stats)
-
-    # parity against the stored oracle values and residuals of the returned pairs
     _, gold = oracle_full_iters()
-    parity = {"max_residual": float(np.max(res)), "converged": converged}
-    if gold is not None:
-        parity["max_rel_err_vs_oracle"] = float(np.max(np.abs(lam - gold) / np.maximum(np.abs(gold), 1.0)))
 
-    # roofline of the dominant kernel: FP64 Gram X^T W (n x 256)^T (n x 256), timed alone, live
-    roof = roofline(pk, solver, w, dev, stream)
-
-    # one timed solve with per-phase timers (paper's profile categories), not part of the timed region
-    phases = None
-    if rank == 0:
+    def run_form(precision, clk_sampler):
+        solver = pk.Solver(V_d, w.N, w.k, w.sbsize, rr_period=w.rr_period, maxiter=args.maxiter, device=dev,
+                           stream=stream, precision=precision)
+        X_out = torch.empty((w.k, w.n), dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            solver.solve(X0_d, w.tol, out=X_out)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        iters, launches, stats = 0, 0, []
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with clk_sampler:
+            ev0.record(stream)
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                lam, _, res, st = solver.solve(X0_d, w.tol, out=X_out)
+                iters += st["iters"]
+                launches += st["kernel_launches"]
+                stats.append(st)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        if dist:
+            dist.barrier()
+        ms = ev0.elapsed_time(ev1)
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        parity = {"max_residual": float(np.max(res)), "converged": all(s_["converged"] == 1 for s_ in stats)}
+        if gold is not None:
+            parity["max_rel_err_vs_oracle"] = float(np.max(np.abs(lam - gold) / np.maximum(np.abs(gold), 1.0)))
+        solver.close()
+        # one more solve with per-phase timers (the paper's profile categories), outside the timed region
         ps = pk.Solver(V_d, w.N, w.k, w.sbsize, rr_period=w.rr_period, maxiter=args.maxiter, device=dev,
-                       stream=stream, timing=True)
+                       stream=stream, timing=True, precision=precision)
         _, _, _, pst = ps.solve(X0_d, w.tol)
-        phases = {k: round(v, 2) for k, v in pst["t_phase_ms"].items()}
         ps.close()
+        return {"ms_per_step": ms / args.steps, "iters": iters // args.steps, "iters_per_s": iters / (ms / 1e3),
+                "wall_s_per_step": wall / args.steps, "launches": launches, "parity": parity,
+                "phase_ms": {k_: round(v_, 2) for k_, v_ in pst["t_phase_ms"].items()},
+                "jacobi_sweeps_max": pst["jacobi_sweeps_max"]}
 
+    clk = ClockSampler(local)
+    fp64 = run_form("fp64", clk)
+    mixed = None if args.no_mixed else run_form("mixed_tf32", ClockSampler(local))
+    ms_per_step = fp64["ms_per_step"]
+    iters = fp64["iters"] * args.steps
+    launches = fp64["launches"]
+    parity = fp64["parity"]
+    phases = fp64["phase_ms"]
+    probe = pk.Solver(V_d, w.N, w.k, w.sbsize, rr_period=w.rr_period, maxiter=1, device=dev, stream=stream)
+    roof = roofline(pk, probe, w, dev, stream)
+    probe.close()
+    roof_mixed = None
+    if mixed is not None:
+        probe = pk.Solver(V_d, w.N, w.k, w.sbsize, rr_period=w.rr_period, maxiter=1, device=dev, stream=stream,
+                          precision="mixed_tf32")
+        roof_mixed = roofline_tc(pk, probe, w, dev, stream)
+        probe.close()
     e2e = None if args.no_e2e else run_e2e(pk, w, V, X0, max(1, args.steps // 2), stream)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -277,13 +287,17 @@ def main():
         "config": {"workload": w.name, "n": w.n, "k": w.k, "sbsize": w.sbsize, "rr_period": w.rr_period,
                    "tol": w.tol, "form": "fp64", "potential": f"{w.n_wells} Gaussian wells + U[0,0.1) noise",
                    "l2": f"no flush: working set {7 * w.n * w.k * 8 / 2**20:.0f} MiB > {L2_BYTES // 2**20} MiB L2"},
-        "iters": iters // args.steps, "iters_per_s": iters / (ms / 1e3), "wall_s_per_step": wall / args.steps,
-        "parity": parity, "roofline": roof, "phase_ms": phases, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": launches, "clocks": clk.summary(),
-        "mixed": {"status": "not built: the FP64 form only (TF32/BF16 projection GEMMs are a later row)"},
+        "iters": fp64["iters"], "iters_per_s": fp64["iters_per_s"], "wall_s_per_step": fp64["wall_s_per_step"],
+        "parity": parity, "roofline": roof, "phase_ms": phases, "jacobi_sweeps_max": fp64["jacobi_sweeps_max"],
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+        "mixed": None if mixed is None else {
+            "form": "TF32 tcgen05 projection GEMMs and first CholeskyQR Gram; everything else FP64",
+            "value": mixed["ms_per_step"] / 1e3, "unit": "s", "iters": mixed["iters"],
+            "iters_per_s": mixed["iters_per_s"], "speedup_vs_fp64": fp64["ms_per_step"] / mixed["ms_per_step"],
+            "parity": mixed["parity"], "phase_ms": mixed["phase_ms"], "gpu_launches": mixed["launches"],
+            "roofline": roof_mixed},
     }
     print(json.dumps(line), flush=True)
-    solver.close()
     if dist:
         dist.destroy_process_group()
     return 0
@@ -313,6 +327,43 @@ def roofline(pk, solver, w, dev, stream):
             "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
             "traffic": ROOFLINE_TRAFFIC_BYTES, "algorithmic_flops_per_launch": flops, "launch_ms": dur * 1e3,
             "peak_note": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)"}
+
+
+def hbm_peak():
+    """Measured HBM copy bandwidth (GB/s) from MEASURED_PEAKS.json, else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def roofline_tc(pk, solver, w, dev, stream):
+    """Mixed form: the tcgen05 TF32 Gram X^T W reads FP64 inputs; HBM is its bound at k = 256."""
+    import torch
+    n, k = w.n, w.k
+    g = torch.Generator(device="cpu").manual_seed(2)
+    A = torch.randn((k, n), generator=g, dtype=torch.float64).to(dev)
+    B = torch.randn((k, n), generator=g, dtype=torch.float64).to(dev)
+    C = torch.empty((k, k), dtype=torch.float64, device=dev)
+    for _ in range(3):
+        pk.ppcg_gram(solver.handle, A.data_ptr(), n, B.data_ptr(), n, k, k, C.data_ptr())
+    reps = 50
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        pk.ppcg_gram(solver.handle, A.data_ptr(), n, B.data_ptr(), n, k, k, C.data_ptr())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dur = e0.elapsed_time(e1) / reps / 1e3
+    nbytes = 8.0 * n * 2 * k
+    peak, kind = hbm_peak()
+    ach = nbytes / dur / 1e9
+    return {"kernel": f"tc_gram_kernel (tcgen05 TF32, + split-K reduce): X^T W, n={n}, {k}x{k}", "bound": "hbm",
+            "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+            "algorithmic_bytes_per_launch": nbytes, "launch_ms": dur * 1e3, "tflops": 2.0 * n * k * k / dur / 1e12,
+            "peak_note": f"{kind} HBM copy bandwidth"}
 
 
 def run_e2e(pk, w, V, X0, steps, stream):

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libppcg.so")
-SOURCES = ["api.cu", "stencil.cu", "gemm.cu", "vec.cu", "blockrr.cu", "dense.cu"]
+SOURCES = ["api.cu", "stencil.cu", "gemm.cu", "vec.cu", "blockrr.cu", "dense.cu", "tcgemm.cu"]
 HEADERS = ["ppcg_internal.h", os.path.join("..", "..", "include", "ppcg.h"),
            os.path.join("..", "..", "include", "ppcg_steps.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

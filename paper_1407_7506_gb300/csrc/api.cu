@@ -53,6 +53,8 @@ struct ppcg_ctx {
   size_t evused = 0;
   double t_ms[8] = {};
   int last_sweeps = 0;
+  bool mixed = false;      // PPCG_MIXED_TF32: projections and the first CholQR Gram on tcgen05
+  int* tcflag = nullptr;   // timeout flag of the tensor-core kernels
 };
 
 namespace {
@@ -142,7 +144,7 @@ ppcg_status check_args(const ppcg_operator* op, int64_t n, int32_t k, int32_t sb
   if (2 * kt > n || kt > 65535) return PPCG_ERR_ARG;
   if (sbsize < 1 || sbsize > kMaxSbsize || sbsize > kt) return PPCG_ERR_ARG;
   if (opt && (opt->maxiter < 0 || opt->sigma_floor < 0.0)) return PPCG_ERR_ARG;
-  if (opt && opt->precision != PPCG_FP64) return PPCG_ERR_UNSUPPORTED;
+  if (opt && opt->precision != PPCG_FP64 && opt->precision != PPCG_MIXED_TF32) return PPCG_ERR_UNSUPPORTED;
   return PPCG_OK;
 }
 
@@ -205,18 +207,34 @@ ppcg_status gram(ppcg_ctx* c, const double* A, int64_t lda, const double* B, int
   return PPCG_OK;
 }
 
-// Y <- Y - X (X^T Y)
+// Gram on the tensor cores (TF32 inputs, FP32 accumulation)
+ppcg_status gram_tc(ppcg_ctx* c, const double* A, int64_t lda, const double* B, int64_t ldb, int ma, int mb,
+                    double* Cm, int ldc) {
+  const bool sym = (A == B && lda == ldb && ma == mb);
+  CK(ppcg::tc_gram(A, lda, B, ldb, c->n, ma, mb, Cm, ldc, sym, c->gpart, c->gpart_cap, c->tcflag, c->stream));
+  return PPCG_OK;
+}
+
+// Steps 9-10: Y <- Y - X (X^T Y); on the tensor cores in the mixed form (the error only perturbs the search
+// direction, whose coefficients the sub-block Rayleigh-Ritz then chooses in FP64)
 ppcg_status project(ppcg_ctx* c, const double* X, int64_t ldx, int mx, double* Y, int64_t ldy, int my) {
   if (mx <= 0 || my <= 0) return PPCG_OK;
+  if (c->mixed) {
+    PS(gram_tc(c, X, ldx, Y, ldy, mx, my, c->G, mx));
+    CK(tc_update(X, ldx, c->G, mx, c->n, mx, my, Y, ldy, true, c->tcflag, c->stream));
+    return PPCG_OK;
+  }
   PS(gram(c, X, ldx, Y, ldy, mx, my, c->G, mx));
   CK(gemm_nn(X, ldx, c->G, mx, c->n, mx, my, Y, ldy, nullptr, 0, Epi::Sub, false, nullptr, c->stream));
   return PPCG_OK;
 }
 
-// One CholQR pass: Xout = Xin R^{-1}, Xin^T Xin + shift I = R^T R
+// One CholQR pass: Xout = Xin R^{-1}, Xin^T Xin + shift I = R^T R. lowprec: the Gram on the tensor cores (first
+// pass of the mixed form); X R^{-1} is always applied in FP64, so span(X) is kept to FP64 accuracy.
 ppcg_status cholqr_pass(ppcg_ctx* c, const double* Xin, int64_t ldi, double* Xout, int64_t ldo, int m,
-                        double shift) {
-  PS(gram(c, Xin, ldi, Xin, ldi, m, m, c->G, m));
+                        double shift, bool lowprec = false) {
+  if (lowprec) PS(gram_tc(c, Xin, ldi, Xin, ldi, m, m, c->G, m));
+  else PS(gram(c, Xin, ldi, Xin, ldi, m, m, c->G, m));
   CK(chol_inv(c->G, m, shift, c->Rinv, c->cholws, c->iflag, c->bar, c->stream));
   CK(gemm_nn(Xin, ldi, c->Rinv, m, c->n, m, m, Xout, ldo, nullptr, 0, Epi::Store, true, nullptr, c->stream));
   return PPCG_OK;
@@ -234,7 +252,7 @@ ppcg_status cholqr2(ppcg_ctx* c, double* X, int64_t ldx, double* Xs, int64_t ldx
   if (fell_back) *fell_back = 0;
   if (m <= 0) return PPCG_OK;
   CK(cudaMemsetAsync(c->iflag, 0, sizeof(int), c->stream));
-  PS(cholqr_pass(c, X, ldx, Xs, ldxs, m, 0.0));
+  PS(cholqr_pass(c, X, ldx, Xs, ldxs, m, 0.0, c->mixed));
   int f = read_flag(c);
   if (f < 0) return PPCG_ERR_CUDA;
   if (f & kFlagTimeout) return PPCG_ERR_TIMEOUT;
@@ -327,9 +345,10 @@ ppcg_status rr_step(ppcg_ctx* c, SolveState& st, bool allow_compact, ppcg_stats*
   // sigma = smallest Ritz value of this step: read lambda first (host needs it for the preconditioner)
   CK(cudaMemcpyAsync(c->lam_h.data(), c->lam, sizeof(double) * kt, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  int fl = 0;
-  CK(cudaMemcpy(&fl, c->iflag, sizeof(int), cudaMemcpyDeviceToHost));
-  if (fl & kFlagTimeout) return PPCG_ERR_TIMEOUT;
+  int fl[3] = {0, 0, 0};
+  CK(cudaMemcpy(&fl[0], c->iflag, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&fl[1], c->tcflag, sizeof(int), cudaMemcpyDeviceToHost));
+  if ((fl[0] | fl[1]) & kFlagTimeout) return PPCG_ERR_TIMEOUT;
   st.sigma = c->lam_h[0];
   if (stats) {
     const int sw = last_sweeps(c);
@@ -501,6 +520,8 @@ ppcg_status ppcg_create(const ppcg_operator* op, int64_t n, int32_t k, int32_t s
   c->cholws = D(o.cholws); c->jacws = D(o.jacws);
   c->iflag = I(o.iflag); c->icnt = I(o.icnt); c->jinfo = I(o.jinfo); c->idx = I(o.idx); c->bflags = I(o.bflags);
   c->bar = reinterpret_cast<unsigned*>(b + o.bar);
+  c->tcflag = c->icnt + 2;
+  c->mixed = (c->opt.precision == PPCG_MIXED_TF32);
   c->lam_h.assign(c->kt, 0.0);
   c->nrm_h.assign(c->kt, 0.0);
   ppcg_status st = ppcg_set_potential(c, op->V);
@@ -672,6 +693,7 @@ ppcg_status ppcg_gram(ppcg_handle c, const double* A, int64_t lda, const double*
                       int32_t mb, double* C) {
   if (!c || !A || !B || !C || ma < 1 || mb < 1 || ma > c->kt || mb > c->kt || lda < c->n || ldb < c->n)
     return PPCG_ERR_ARG;
+  if (c->mixed) return gram_tc(c, A, lda, B, ldb, ma, mb, C, ma);
   return gram(c, A, lda, B, ldb, ma, mb, C, ma);
 }
 

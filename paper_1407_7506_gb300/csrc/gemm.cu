@@ -221,6 +221,16 @@ cudaError_t gram(const double* A, int64_t lda, const double* B, int64_t ldb, int
   return cudaGetLastError();
 }
 
+cudaError_t gram_reduce_partials(const double* part, int nsplit, int ma, int mb, double* C, int ldc, bool symmetric,
+                                 cudaStream_t s) {
+  const int64_t total = (int64_t)ma * mb;
+  const int64_t blocks = ceil_div(total, 256);
+  gram_reduce_kernel<<<(unsigned)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(part, nsplit, ma, mb, C, ldc,
+                                                                                symmetric ? 1 : 0);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t gemm_nn(const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p, double* Y,
                     int64_t ldy, const double* Yin, int64_t ldyin, Epi epi, bool g_upper, const ResidualArgs* ra,
                     cudaStream_t s) {

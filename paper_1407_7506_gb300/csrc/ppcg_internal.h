@@ -21,7 +21,7 @@ constexpr int kMaxSbsize = 16;          // 3q <= 48 fits the warp-level sub-bloc
 // Error-flag bits written by kernels into the handle's device flag word.
 enum : int { kFlagCholBreakdown = 1, kFlagTimeout = 2, kFlagJacobiNoConv = 4 };
 
-inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // Process-wide count of kernels launched by this library (reported per solve in ppcg_stats).
 void count_launch(int n = 1);
@@ -60,6 +60,17 @@ cudaError_t gemm_nn(const double* A, int64_t lda, const double* G, int ldg, int6
                     int64_t ldy, const double* Yin, int64_t ldyin, Epi epi, bool g_upper, const ResidualArgs* ra,
                     cudaStream_t s);
 int64_t norm_row_tiles(int64_t n);   // row tiles of gemm_nn / residual_diag (norm_part has this many rows)
+// sum FP64 split-K partials part[split][i + j*ma] into C (mirrored when symmetric)
+cudaError_t gram_reduce_partials(const double* part, int nsplit, int ma, int mb, double* C, int ldc, bool symmetric,
+                                 cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------------- tcgen05 (TF32)
+// Same contracts as gram / gemm_nn (Sub or Store), with TF32 inputs and FP32 accumulation on the tensor cores.
+// *flag receives kFlagTimeout if a bounded mbarrier wait gave up.
+cudaError_t tc_gram(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n, int ma, int mb, double* C,
+                    int ldc, bool symmetric, double* part, size_t part_capacity, int* flag, cudaStream_t s);
+cudaError_t tc_update(const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p, double* Y,
+                      int64_t ldy, bool subtract, int* flag, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------------------- vectors
 // R = HX - X diag(lam); W = T R; norm_part per row tile.

@@ -1,0 +1,404 @@
+// Tensor-core (tcgen05, TF32 inputs, FP32 accumulation in TMEM) versions of the tall-skinny GEMMs whose
+// rounding only perturbs search directions: the projections of steps 9-10 (G = X^T W, W <- W - X G) and the
+// Gram of the first CholeskyQR pass (its error changes only the conditioning of R, not span(X), because
+// X R^{-1} is applied in FP64). This is the mixed-precision form of the method's workload.
+//
+// The blocks are FP64 in HBM, which TMA cannot convert, so the operand tiles are staged by the threads: coalesced
+// FP64 loads, conversion to TF32 (round to nearest), and stores into shared memory in the canonical K-major
+// layout without swizzle (core matrices of 8 rows x 16 bytes; LBO = 128 B between core matrices along K,
+// SBO = 1024 B between 8-row groups). One thread issues tcgen05.mma (M = 128, N = NT, K = 8 per instruction) into
+// a TMEM accumulator and commits to an mbarrier per stage; two stages overlap staging with the MMAs. The epilogue
+// reads TMEM with tcgen05.ld (each warp its 32-lane quadrant) and writes FP64.
+//
+//   tc_gram    C = A^T B split over row chunks into FP64 partials (summed by the FP64 Gram reduce kernel)
+//   tc_update  Y = Y - A G (or Y = A G)
+//
+// Every mbarrier wait is bounded; on timeout the CTA records kFlagTimeout, waits (bounded) once more for its
+// MMAs, frees its TMEM and returns.
+#include "ppcg_internal.h"
+
+#include <algorithm>
+
+namespace ppcg {
+
+// FP64 Gram reduce kernel launcher (gemm.cu)
+cudaError_t gram_reduce_partials(const double* part, int nsplit, int ma, int mb, double* C, int ldc, bool symmetric,
+                                 cudaStream_t s);
+
+namespace {
+
+constexpr int kM = 128;           // MMA M: rows of the accumulator = TMEM lanes
+constexpr int kBK = 32;           // K elements staged per stage (4 MMAs of K = 8)
+constexpr int kThreads = 256;     // 8 warps
+constexpr uint32_t kLBO = 128;    // bytes between core matrices along K
+constexpr uint32_t kSBO = 1024;   // bytes between 8-row groups (kBK / 4 core matrices of 128 B)
+constexpr long long kMbarSpin = 1LL << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// byte offset of element (row, k) in a K-major no-swizzle tile
+__device__ __forceinline__ uint32_t tile_off(int row, int k) {
+  return (uint32_t)(row >> 3) * kSBO + (uint32_t)(row & 7) * 16u + (uint32_t)(k >> 2) * kLBO + (uint32_t)(k & 3) * 4u;
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((kLBO >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((kSBO >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;          // descriptor version of tcgen05; base offset 0; no swizzle
+  return d;
+}
+
+// instruction descriptor of tcgen05.mma .kind::tf32: D = F32, A = B = TF32, both K-major, N >> 3, M >> 4
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ float to_tf32(double x) {
+  uint32_t r;
+  const float f = (float)x;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+  for (long long i = 0; i < kMbarSpin; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot_addr, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot_addr), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar_addr) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_addr)
+               : "memory");
+}
+
+// 16 consecutive 32-bit TMEM columns of this thread's lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcSmem {
+  uint64_t mbar[2];
+  uint32_t tmem_slot;
+  int ok;
+};
+
+// Shared machinery: K loop over nk stages of kBK, staging by `stage(kb, a_tile, b_tile)`, MMAs by thread 0.
+// Returns false (uniformly) if a bounded wait gave up; TMEM is still allocated on return (caller frees it).
+template <class StageFn>
+__device__ bool tc_mainloop(int nk, uint8_t* tiles, uint32_t a_bytes, uint32_t b_bytes, TcSmem& sm, uint32_t tmem,
+                            uint32_t idesc, StageFn stage) {
+  const int tid = threadIdx.x;
+  const uint32_t stage_bytes = a_bytes + b_bytes;
+  for (int kb = 0; kb < nk; ++kb) {
+    const int s = kb & 1;
+    uint8_t* a_tile = tiles + s * stage_bytes;
+    uint8_t* b_tile = a_tile + a_bytes;
+    if (kb >= 2) {
+      // the MMAs of step kb-2 used this stage: wait for their commit (completion number (kb-2)/2)
+      if (tid == 0) sm.ok = mbar_wait(smem_u32(&sm.mbar[s]), (uint32_t)(((kb - 2) >> 1) & 1)) ? 1 : 0;
+      __syncthreads();
+      if (!sm.ok) return false;
+    }
+    stage(kb, a_tile, b_tile);
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(a_tile), b0 = smem_u32(b_tile);
+#pragma unroll
+      for (int j = 0; j < kBK / 8; ++j)
+        mma_tf32(tmem, smem_desc(a0 + j * 2 * kLBO), smem_desc(b0 + j * 2 * kLBO), idesc,
+                 (kb > 0 || j > 0) ? 1u : 0u);
+      mma_commit(smem_u32(&sm.mbar[s]));
+    }
+  }
+  if (nk > 0) {
+    const int last = nk - 1;
+    if (tid == 0) sm.ok = mbar_wait(smem_u32(&sm.mbar[last & 1]), (uint32_t)((last >> 1) & 1)) ? 1 : 0;
+    __syncthreads();
+    if (!sm.ok) return false;
+  }
+  tc_fence_after();
+  return true;
+}
+
+__device__ void tc_setup(TcSmem& sm, uint32_t ncols) {
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&sm.mbar[0]), 1);
+    mbar_init(smem_u32(&sm.mbar[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (threadIdx.x / 32 == 0) tmem_alloc(smem_u32(&sm.tmem_slot), ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+}
+
+__device__ void tc_teardown(TcSmem& sm, uint32_t tmem, uint32_t ncols, bool ok, int nk, int* flag) {
+  if (!ok) {
+    // a bounded wait gave up: record it and give the in-flight MMAs one more bounded wait before freeing TMEM
+    if (threadIdx.x == 0) {
+      atomicOr(flag, kFlagTimeout);
+      if (nk > 0) mbar_wait(smem_u32(&sm.mbar[(nk - 1) & 1]), (uint32_t)(((nk - 1) >> 1) & 1));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x / 32 == 0) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, ncols);
+  }
+}
+
+// ------------------------------------------------------------------------------------------ C = A^T B partials
+// grid (tiles_m * tiles_n, nsplit); tile rows m0 = tm * 128 (columns of A), cols n0 = tn * NT (columns of B)
+__global__ void __launch_bounds__(kThreads, 1)
+tc_gram_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ B, int64_t ldb, int64_t n,
+               int ma, int mb, int NT, int tiles_n, int64_t rows_per_split, double* __restrict__ part, int* flag) {
+  extern __shared__ __align__(1024) uint8_t dyn[];
+  __shared__ TcSmem sm;
+  const int tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
+  const int m0 = tm * kM, n0 = tn * NT;
+  const int64_t r_begin = (int64_t)blockIdx.y * rows_per_split;
+  const int64_t r_end = min(n, r_begin + rows_per_split);
+  const int nk = r_end > r_begin ? (int)ceil_div(r_end - r_begin, kBK) : 0;
+  const uint32_t a_bytes = (kM / 8) * kSBO, b_bytes = (uint32_t)(NT / 8) * kSBO;
+  const uint32_t ncols = (uint32_t)NT;
+  tc_setup(sm, ncols);
+  const uint32_t tmem = sm.tmem_slot;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  const int mm = lane >> 2, kk = lane & 3;        // position inside a core matrix (8 rows x 4 k)
+  auto stage = [&](int kb, uint8_t* a_tile, uint8_t* b_tile) {
+    const int64_t r0 = r_begin + (int64_t)kb * kBK;
+    // A tile: 128 rows (columns of A) x 32 k (rows of A); core matrix (g, c) covers rows 8g.., k 4c..
+    for (int cm = warp; cm < (kM / 8) * (kBK / 4); cm += kThreads / 32) {
+      const int g = cm / (kBK / 4), c = cm % (kBK / 4);
+      const int row = 8 * g + mm, k = 4 * c + kk;
+      const int64_t gr = r0 + k;
+      const int gc = m0 + row;
+      const double v = (gr < r_end && gc < ma) ? __ldg(A + gr + (int64_t)gc * lda) : 0.0;
+      *reinterpret_cast<float*>(a_tile + tile_off(row, k)) = to_tf32(v);
+    }
+    for (int cm = warp; cm < (NT / 8) * (kBK / 4); cm += kThreads / 32) {
+      const int g = cm / (kBK / 4), c = cm % (kBK / 4);
+      const int row = 8 * g + mm, k = 4 * c + kk;
+      const int64_t gr = r0 + k;
+      const int gc = n0 + row;
+      const double v = (gr < r_end && gc < mb) ? __ldg(B + gr + (int64_t)gc * ldb) : 0.0;
+      *reinterpret_cast<float*>(b_tile + tile_off(row, k)) = to_tf32(v);
+    }
+  };
+  const bool ok = tc_mainloop(nk, dyn, a_bytes, b_bytes, sm, tmem, idesc_tf32(kM, NT), stage);
+  if (ok) {
+    // epilogue: warp w reads lanes 32 (w % 4).., columns [h NT/2, (h+1) NT/2) with h = w / 4
+    double* out = part + (int64_t)blockIdx.y * ma * mb;
+    const int q = warp & 3, h = warp >> 2;
+    const int row = 32 * q + lane;
+    const int gi = m0 + row;
+    for (int c0 = h * (NT / 2); c0 < (h + 1) * (NT / 2); c0 += 16) {
+      float v[16];
+      if (nk > 0) tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+      else
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+      if (gi < ma) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int gj = n0 + c0 + i;
+          if (gj < mb) out[gi + (int64_t)gj * ma] = (double)v[i];
+        }
+      }
+    }
+  }
+  tc_teardown(sm, tmem, ncols, ok, nk, flag);
+}
+
+// ------------------------------------------------------------------------------------------ Y = Y - A G / Y = A G
+// grid (ceil(n / 128), ceil(p / NT)); A: n x m, G: m x p, Y: n x p
+__global__ void __launch_bounds__(kThreads, 1)
+tc_update_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ G, int ldg, int64_t n, int m,
+                 int p, int NT, double* Y, int64_t ldy, int subtract, int* flag) {
+  extern __shared__ __align__(1024) uint8_t dyn[];
+  __shared__ TcSmem sm;
+  const int64_t r0 = (int64_t)blockIdx.x * kM;
+  const int c0 = blockIdx.y * NT;
+  const int nk = (int)ceil_div(m, kBK);
+  const uint32_t a_bytes = (kM / 8) * kSBO, b_bytes = (uint32_t)(NT / 8) * kSBO;
+  const uint32_t ncols = (uint32_t)NT;
+  tc_setup(sm, ncols);
+  const uint32_t tmem = sm.tmem_slot;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  auto stage = [&](int kb, uint8_t* a_tile, uint8_t* b_tile) {
+    const int k0 = kb * kBK;
+    // A tile (rows of A x k): lanes run down the rows (coalesced), core matrix (g, c)
+    const int ar = lane & 7, ak = lane >> 3;
+    for (int cm = warp; cm < (kM / 8) * (kBK / 4); cm += kThreads / 32) {
+      const int g = cm % (kM / 8), c = cm / (kM / 8);
+      const int row = 8 * g + ar, k = 4 * c + ak;
+      const int64_t gr = r0 + row;
+      const int gk = k0 + k;
+      const double v = (gr < n && gk < m) ? __ldg(A + gr + (int64_t)gk * lda) : 0.0;
+      *reinterpret_cast<float*>(a_tile + tile_off(row, k)) = to_tf32(v);
+    }
+    // B tile (columns of G x k): lanes run along k (contiguous in G)
+    const int bn = lane >> 2, bk = lane & 3;
+    for (int cm = warp; cm < (NT / 8) * (kBK / 4); cm += kThreads / 32) {
+      const int g = cm / (kBK / 4), c = cm % (kBK / 4);
+      const int row = 8 * g + bn, k = 4 * c + bk;
+      const int gk = k0 + k;
+      const int gc = c0 + row;
+      const double v = (gk < m && gc < p) ? __ldg(G + gk + (int64_t)gc * ldg) : 0.0;
+      *reinterpret_cast<float*>(b_tile + tile_off(row, k)) = to_tf32(v);
+    }
+  };
+  const bool ok = tc_mainloop(nk, dyn, a_bytes, b_bytes, sm, tmem, idesc_tf32(kM, NT), stage);
+  if (ok) {
+    const int q = warp & 3, h = warp >> 2;
+    const int64_t gr = r0 + 32 * q + lane;
+    for (int cc = h * (NT / 2); cc < (h + 1) * (NT / 2); cc += 16) {
+      float v[16];
+      if (nk > 0) tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)cc, v);
+      else
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+      if (gr < n) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int gc = c0 + cc + i;
+          if (gc < p) {
+            double* y = Y + gr + (int64_t)gc * ldy;
+            *y = subtract ? (*y - (double)v[i]) : (double)v[i];
+          }
+        }
+      }
+    }
+  }
+  tc_teardown(sm, tmem, ncols, ok, nk, flag);
+}
+
+int pick_nt(int cols) {
+  if (cols <= 32) return 32;
+  if (cols <= 64) return 64;
+  if (cols <= 128) return 128;
+  return 256;
+}
+
+size_t tc_smem_bytes(int NT) { return 2 * ((size_t)(kM / 8) * kSBO + (size_t)(NT / 8) * kSBO) + 1024; }
+
+// Sets the dynamic shared memory of fn to at least `bytes`, padded so that no more CTAs than 512 / NT can be
+// resident on one SM: tcgen05.alloc waits for free TMEM columns, and the SM has 512.
+cudaError_t set_smem(const void* fn, size_t& bytes, int NT) {
+  const int max_ctas = 512 / NT;
+  for (int tries = 0; tries < 8; ++tries) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, bytes);
+    if (e != cudaSuccess) return e;
+    if (per_sm <= max_ctas) return cudaSuccess;
+    bytes = std::min<size_t>(bytes * 2, 200 * 1024);
+  }
+  return cudaErrorInvalidConfiguration;
+}
+
+int sm_count() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+}  // namespace
+
+cudaError_t tc_gram(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n, int ma, int mb, double* C,
+                    int ldc, bool symmetric, double* part, size_t part_capacity, int* flag, cudaStream_t s) {
+  if (ma <= 0 || mb <= 0) return cudaSuccess;
+  if ((size_t)ma * mb > part_capacity) return cudaErrorInvalidValue;
+  const int NT = pick_nt(mb);
+  const int tiles_m = (int)ceil_div(ma, kM), tiles_n = (int)ceil_div(mb, NT);
+  const int tiles = tiles_m * tiles_n;
+  // enough CTAs to pull from HBM, while the FP64 partials stay below ~1/4 of the input bytes
+  int64_t nsplit = ceil_div(2LL * sm_count(), tiles);
+  const int64_t cap_traffic = (n * (int64_t)(ma + mb)) / (4LL * ma * mb) + 1;
+  const int64_t cap_rows = ceil_div(n, 4 * kBK);
+  const int64_t cap_mem = (int64_t)(part_capacity / ((size_t)ma * mb));
+  nsplit = std::min(nsplit, std::min(cap_traffic, std::min(cap_rows, cap_mem)));
+  if (nsplit < 1) nsplit = 1;
+  int64_t rows = ceil_div(ceil_div(n, nsplit), kBK) * kBK;
+  const int nsp = (int)ceil_div(n, rows);
+  size_t smem = tc_smem_bytes(NT);
+  cudaError_t e = set_smem((const void*)tc_gram_kernel, smem, NT);
+  if (e != cudaSuccess) return e;
+  tc_gram_kernel<<<dim3(tiles, nsp), kThreads, smem, s>>>(A, lda, B, ldb, n, ma, mb, NT, tiles_n, rows, part, flag);
+  count_launch();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return gram_reduce_partials(part, nsp, ma, mb, C, ldc, symmetric, s);
+}
+
+cudaError_t tc_update(const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p, double* Y,
+                      int64_t ldy, bool subtract, int* flag, cudaStream_t s) {
+  if (p <= 0 || n <= 0) return cudaSuccess;
+  const int NT = pick_nt(p);
+  size_t smem = tc_smem_bytes(NT);
+  cudaError_t e = set_smem((const void*)tc_update_kernel, smem, NT);
+  if (e != cudaSuccess) return e;
+  tc_update_kernel<<<dim3((unsigned)ceil_div(n, kM), (unsigned)ceil_div(p, NT)), kThreads, smem, s>>>(
+      A, lda, G, ldg, n, m, p, NT, Y, ldy, subtract ? 1 : 0, flag);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace ppcg

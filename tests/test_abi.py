@@ -93,7 +93,7 @@ def test_unsupported_options_are_reported(lib):
     out = ctypes.c_size_t(0)
     assert lib.ppcg_workspace_bytes(ctypes.byref(op), 4096, 8, 2, None, ctypes.byref(out)) == pk.PPCG_ERR_UNSUPPORTED
     opt = pk.ppcg_options()
-    opt.precision = 1
+    opt.precision = 2                                   # BF16 mixed form: not provided
     assert (lib.ppcg_workspace_bytes(ctypes.byref(_op(16)), 4096, 8, 2, ctypes.byref(opt), ctypes.byref(out))
             == pk.PPCG_ERR_UNSUPPORTED)
 

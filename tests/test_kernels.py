@@ -281,3 +281,48 @@ def test_residual_preconditioned(use_M):
         W, nrm = host(Wd), nd.cpu().numpy()
     np.testing.assert_allclose(W, ref_W, rtol=0, atol=1e-12 * np.max(np.abs(ref_W)))
     np.testing.assert_allclose(nrm, np.sum(R * R, axis=0), rtol=1e-10)
+
+
+# ------------------------------------------------------------------------------------- mixed form: tcgen05 TF32
+U_TF32 = 2.0 ** -11          # unit roundoff of TF32 (10 explicit mantissa bits, round to nearest)
+
+
+@pytest.mark.parametrize("N,ma,mb,sym", [(5, 37, 61, False), (10, 70, 130, False), (16, 256, 256, False),
+                                         (16, 130, 130, True), (16, 200, 33, False), (10, 1, 1, False)])
+def test_gram_tensor_core_tf32(N, ma, mb, sym):
+    n = N ** 3
+    rng = _rng(ma * 1000 + mb + 7)
+    A = rng.standard_normal((n, ma))
+    B = A if sym else rng.standard_normal((n, mb))
+    with Handle(np.zeros(n), N, kt=max(ma, mb), sbsize=1, precision=1) as H:
+        Ad = dev(A)
+        Bd = Ad if sym else dev(B)
+        Cd = torch.empty((mb, ma), dtype=torch.float64, device="cuda")
+        pk.ppcg_gram(H.h, ptr(Ad), n, ptr(Bd), n, ma, mb, ptr(Cd))
+        C = host(Cd)
+    ref = A.T @ B
+    # each product carries two TF32 roundings; FP32 accumulation over a chunk adds far less
+    bound = (2.2 * U_TF32 + 1e-5) * (np.abs(A).T @ np.abs(B))
+    assert np.all(np.abs(C - ref) <= bound), np.max(np.abs(C - ref) / bound)
+    assert np.max(np.abs(C - ref)) > 0            # it really ran in reduced precision
+    if sym:
+        np.testing.assert_array_equal(C, C.T)
+
+
+@pytest.mark.parametrize("N,mx,my", [(11, 40, 25), (16, 256, 256), (16, 130, 70)])
+def test_project_tensor_core_tf32(N, mx, my):
+    n = N ** 3
+    rng = _rng(mx + my)
+    X = oracle.cholqr2(rng.standard_normal((n, mx)))[0]
+    Y = rng.standard_normal((n, my))
+    with Handle(np.zeros(n), N, kt=max(mx, my), sbsize=1, precision=1) as H:
+        Xd, Yd = dev(X), dev(Y)
+        pk.ppcg_project(H.h, ptr(Xd), n, mx, ptr(Yd), n, my)
+        Z = host(Yd)
+    ref = oracle.project(Y, X)
+    # G = X^T Y has TF32 errors ~ 2u |X|^T |Y|; W - X G adds ~ 2u |X| |G|
+    G_abs = np.abs(X).T @ np.abs(Y)
+    bound = 2.2 * U_TF32 * (np.abs(X) @ G_abs) * 2 + 1e-12
+    assert np.all(np.abs(Z - ref) <= bound)
+    # the projection still removes span(X) up to the TF32 level
+    assert np.max(np.abs(X.T @ Z)) < 50 * U_TF32 * np.max(np.abs(Y)) * np.sqrt(n)

@@ -25,8 +25,9 @@ def _gpu():
     need_gpu()
 
 
-def _gpu_solve(V, N, k, q, rr, X0, tol=1e-8, nbuf=0, lock=True, maxiter=3000, history=0):
-    s = pk.Solver(V, N, k, q, rr_period=rr, nbuf=nbuf, lock=lock, maxiter=maxiter, history=history)
+def _gpu_solve(V, N, k, q, rr, X0, tol=1e-8, nbuf=0, lock=True, maxiter=3000, history=0, precision="fp64"):
+    s = pk.Solver(V, N, k, q, rr_period=rr, nbuf=nbuf, lock=lock, maxiter=maxiter, history=history,
+                  precision=precision)
     try:
         lam, X, res, st = s.solve(X0, tol)
         return lam, X.cpu().numpy().T.copy(), res, st
@@ -109,6 +110,31 @@ def test_iteration_history_tracks_oracle(N, k, q):
     assert np.all(rel <= 1e-4), rel
     tr = g[:early, 1] == 1
     np.testing.assert_allclose(g[:early][tr, 3], o[:early][tr, 3], rtol=1e-12)
+
+
+LAM_TOL_MIXED = 1e-9
+
+
+@pytest.mark.parametrize("N,k,q", [(8, 8, 2), (10, 20, 6), (9, 12, 3)])
+def test_mixed_form_solve(N, k, q):
+    # TF32 projections and first CholQR Gram on the tensor cores; every pair still reaches residual 1e-8
+    w = wl.small("mx", N=N, k=k, sbsize=q, seed=70 + N + k)
+    V, X0 = wl.make_inputs(w)
+    lam, X, res, st = _gpu_solve(V, N, k, q, 5, X0, precision="mixed")
+    assert st["status"] == "ok" and st["converged"] == 1, st
+    _check_pairs(V, N, lam, X, 1e-8)
+    ev = np.linalg.eigvalsh(oracle.assemble_H(V, N, 1.0))[:k]
+    assert np.all(_rel(lam, ev) <= LAM_TOL_MIXED), np.max(_rel(lam, ev))
+
+
+def test_mixed_form_config1_against_dense_golden():
+    w = wl.CONFIGS[1]
+    V, X0 = wl.make_inputs(w)
+    gold = np.loadtxt(os.path.join(GOLDEN, "config1_dense_eigs.txt"))[:w.k]
+    lam, X, res, st = _gpu_solve(V, w.N, w.k, w.sbsize, w.rr_period, X0, tol=w.tol, maxiter=5000, precision="mixed")
+    assert st["converged"] == 1, st
+    assert np.all(_rel(lam, gold) <= LAM_TOL_MIXED), np.max(_rel(lam, gold))
+    _check_pairs(V, w.N, lam, X, w.tol)
 
 
 def test_solve_k1():
