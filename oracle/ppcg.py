@@ -16,8 +16,8 @@ Readings of the paper taken where it is silent (each is restated where it is use
   R3  P is kept per column position across a Rayleigh-Ritz step: the new active column at sorted position i
       takes the conjugate direction that belonged to position i (Alg. 3 step 28, "P <- P(J_act)"); a position
       that was locked carries a zero direction.
-  R4  the Rayleigh-Ritz step on S = [X, X_lock] (Alg. 3 steps 22-24) orthonormalises S by CholQR2 and solves
-      the standard eigenproblem of Q* A Q, which has the same Ritz pairs as the generalised eq. (projev).
+  R4  the Rayleigh-Ritz step on S = [X, X_lock] (Alg. 3 steps 22-24) solves the generalised eq. (projev) on S
+      as written (Cholesky reduction of S* S); only if that Cholesky breaks down is S orthonormalised first.
   R5  Cholesky factor R of X*X is upper triangular with a positive diagonal (the text's "unit upper" cannot
       hold for a Cholesky factor); CholQR is applied twice (CholeskyQR2); on breakdown (a relative pivot
       R_ii / sqrt(G_ii) < CHOL_PIVOT_TOL) the shifted CholeskyQR3 of Fukaya, Kannan, Nakatsukasa, Yamamoto,
@@ -251,12 +251,29 @@ def block_update(Xj, Wj, Pj, CX, CW, CP):
 
 
 def rayleigh_ritz(S, Hop, stats=None):
-    """Steps 22-24 (reading R4): Q = orth(S); M = Q* A Q; M C = C Omega (ascending); X = Q C."""
-    Q = orth(S, stats)
-    M = Q.conj().T @ Hop(Q)
-    M = 0.5 * (M + M.conj().T)
-    Omega, C = np.linalg.eigh(M)
-    return np.asfortranarray(Q @ C), Omega
+    """Steps 22-24 (reading R4): eq. projev on S = [X, X_lock] as written, (S* A S) C = (S* S) C Omega with
+    C* (S* S) C = I, Omega ascending; X = S C. Solved by LAPACK's generalised driver (Cholesky reduction of
+    S* S to standard form). If that Cholesky breaks down (relative pivot below CHOL_PIVOT_TOL, as in CholQR),
+    S is orthonormalised first and the standard problem Q* A Q is solved instead (same Ritz pairs)."""
+    HS = Hop(S)
+    GA = S.conj().T @ HS
+    GB = S.conj().T @ S
+    GA = 0.5 * (GA + GA.conj().T)
+    GB = 0.5 * (GB + GB.conj().T)
+    try:
+        L = np.linalg.cholesky(GB)
+        if np.min(np.real(np.diag(L)) / np.sqrt(np.real(np.diag(GB)))) < CHOL_PIVOT_TOL:
+            raise np.linalg.LinAlgError("Rayleigh-Ritz Gram breakdown")
+        Omega, C = sla.eigh(GA, GB)
+        return np.asfortranarray(S @ C), Omega
+    except np.linalg.LinAlgError:
+        if stats is not None:
+            stats["n_cholqr_fallback"] += 1
+        Q = orth(S, stats)
+        M = Q.conj().T @ Hop(Q)
+        M = 0.5 * (M + M.conj().T)
+        Omega, C = np.linalg.eigh(M)
+        return np.asfortranarray(Q @ C), Omega
 
 
 def residual(X, HX, M):

@@ -326,29 +326,54 @@ struct SolveState {
 };
 
 // Steps 22-31: Rayleigh-Ritz on S = [X_lock, X_act], residuals, stop test, locking and compaction.
+// Step 23 solves eq. projev on S as written: with S^T S = R^T R (Cholesky), K = R^{-T} (S^T A S) R^{-1} is
+// diagonalised by Jacobi, K Z = Z Omega, and X = S (R^{-1} Z). If that Cholesky breaks down (relative pivot below
+// kCholPivotTol), S is orthonormalised by CholeskyQR2 first and the standard problem Q^T A Q is solved instead.
 ppcg_status rr_step(ppcg_ctx* c, SolveState& st, bool allow_compact, ppcg_stats* stats, double tol) {
   const int kt = c->kt;
-  phase_mark(c, PPCG_T_RR);
-  int fb = 0;
-  PS(cholqr2(c, c->X, c->ld, c->Xs, c->ld, kt, &fb));
-  if (fb && stats) stats->n_cholqr_fallback++;
+  cudaStream_t s = c->stream;
+  int* rrflag = c->icnt + 3;
   phase_mark(c, PPCG_T_AX);
   PS(apply_H(c, c->X, c->ld, c->HX, c->ld, kt));
   phase_mark(c, PPCG_T_RR);
-  PS(gram(c, c->X, c->ld, c->HX, c->ld, kt, kt, c->M, kt));
+  PS(gram(c, c->X, c->ld, c->X, c->ld, kt, kt, c->G, kt));              // S^T S
+  PS(gram(c, c->X, c->ld, c->HX, c->ld, kt, kt, c->M, kt));             // S^T A S
+  CK(cudaMemsetAsync(rrflag, 0, sizeof(int), s));
+  CK(chol_inv(c->G, kt, 0.0, c->Rinv, c->cholws, rrflag, c->bar, s));  // R^{-1}
+  // K = R^{-T} (S^T A S) R^{-1}: T = (S^T A S) R^{-1} (R^{-1} upper: trimmed K loop), K = (R^{-1})^T T
+  CK(gemm_nn(c->M, kt, c->Rinv, kt, kt, kt, kt, c->G, kt, nullptr, 0, Epi::Store, true, nullptr, s));
+  CK(ppcg::gram(c->Rinv, kt, c->G, kt, kt, kt, kt, c->M, kt, false, c->gpart, c->gpart_cap, s));
   PS(dense_eigh(c, c->M, kt, c->lam, c->C));
-  CK(gemm_nn(c->X, c->ld, c->C, kt, c->n, kt, kt, c->Xs, c->ld, nullptr, 0, Epi::Store, false, nullptr, c->stream));
+  // sigma = smallest Ritz value of this step: the host needs it for the preconditioner
+  CK(cudaMemcpyAsync(c->lam_h.data(), c->lam, sizeof(double) * kt, cudaMemcpyDeviceToHost, s));
+  int fl[3] = {0, 0, 0};
+  CK(cudaMemcpyAsync(&fl[0], c->iflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&fl[1], c->tcflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&fl[2], rrflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if ((fl[0] | fl[1] | fl[2]) & kFlagTimeout) return PPCG_ERR_TIMEOUT;
+  if (fl[2] & kFlagCholBreakdown) {
+    // S^T S too ill-conditioned for the reduction: orthonormalise S and solve the standard problem
+    if (stats) stats->n_cholqr_fallback++;
+    int fb = 0;
+    PS(cholqr2(c, c->X, c->ld, c->Xs, c->ld, kt, &fb));
+    PS(apply_H(c, c->X, c->ld, c->HX, c->ld, kt));
+    PS(gram(c, c->X, c->ld, c->HX, c->ld, kt, kt, c->M, kt));
+    PS(dense_eigh(c, c->M, kt, c->lam, c->C));
+    CK(cudaMemcpyAsync(c->G, c->C, sizeof(double) * (size_t)kt * kt, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c->lam_h.data(), c->lam, sizeof(double) * kt, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&fl[0], c->iflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (fl[0] & kFlagTimeout) return PPCG_ERR_TIMEOUT;
+  } else {
+    // coefficients R^{-1} Z (R^{-1} is upper triangular)
+    CK(gemm_nn(c->Rinv, kt, c->C, kt, kt, kt, kt, c->G, kt, nullptr, 0, Epi::Store, false, nullptr, s));
+  }
+  CK(gemm_nn(c->X, c->ld, c->G, kt, c->n, kt, kt, c->Xs, c->ld, nullptr, 0, Epi::Store, false, nullptr, s));
   swap(c->X, c->Xs);
   phase_mark(c, PPCG_T_AX);
   PS(apply_H(c, c->X, c->ld, c->HX, c->ld, kt));
   phase_mark(c, PPCG_T_PRECOND);
-  // sigma = smallest Ritz value of this step: read lambda first (host needs it for the preconditioner)
-  CK(cudaMemcpyAsync(c->lam_h.data(), c->lam, sizeof(double) * kt, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  int fl[3] = {0, 0, 0};
-  CK(cudaMemcpy(&fl[0], c->iflag, sizeof(int), cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(&fl[1], c->tcflag, sizeof(int), cudaMemcpyDeviceToHost));
-  if ((fl[0] | fl[1]) & kFlagTimeout) return PPCG_ERR_TIMEOUT;
   st.sigma = c->lam_h[0];
   if (stats) {
     const int sw = last_sweeps(c);
