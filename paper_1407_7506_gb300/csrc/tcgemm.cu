@@ -128,13 +128,16 @@ struct TcSmem {
   int ok;
 };
 
-// Shared machinery: K loop over nk stages of kBK, staging by `stage(kb, a_tile, b_tile)`, MMAs by thread 0.
+// Shared machinery: K loop over nk stages of kBK. `load(kb)` issues the global loads of stage kb into registers,
+// `store(a_tile, b_tile)` converts and writes them; thread 0 issues the MMAs. The loads of stage kb+1 are in flight
+// while stage kb's MMAs are issued and while the loop waits for the buffer it is about to overwrite.
 // Returns false (uniformly) if a bounded wait gave up; TMEM is still allocated on return (caller frees it).
-template <class StageFn>
+template <class LoadFn, class StoreFn>
 __device__ bool tc_mainloop(int nk, uint8_t* tiles, uint32_t a_bytes, uint32_t b_bytes, TcSmem& sm, uint32_t tmem,
-                            uint32_t idesc, StageFn stage) {
+                            uint32_t idesc, LoadFn load, StoreFn store) {
   const int tid = threadIdx.x;
   const uint32_t stage_bytes = a_bytes + b_bytes;
+  if (nk > 0) load(0);
   for (int kb = 0; kb < nk; ++kb) {
     const int s = kb & 1;
     uint8_t* a_tile = tiles + s * stage_bytes;
@@ -145,7 +148,8 @@ __device__ bool tc_mainloop(int nk, uint8_t* tiles, uint32_t a_bytes, uint32_t b
       __syncthreads();
       if (!sm.ok) return false;
     }
-    stage(kb, a_tile, b_tile);
+    store(a_tile, b_tile);
+    if (kb + 1 < nk) load(kb + 1);
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
@@ -198,11 +202,23 @@ __device__ void tc_teardown(TcSmem& sm, uint32_t tmem, uint32_t ncols, bool ok, 
   }
 }
 
+// Per-thread register staging. A warp stages whole core matrices (8 rows x 4 k = 32 elements, one per lane), so
+// its shared-memory stores fill 128 contiguous bytes. All global loads of a stage are issued before any is
+// converted and stored, and the next stage's loads are issued while the MMAs run.
+template <int NT>
+struct Stage {
+  static constexpr int kA = (kM / 8) * (kBK / 4) / (kThreads / 32);   // core matrices of A per warp (16)
+  static constexpr int kB = (NT / 8) * (kBK / 4) / (kThreads / 32);   // core matrices of B per warp
+  double a[kA];
+  double b[kB];
+};
+
 // ------------------------------------------------------------------------------------------ C = A^T B partials
 // grid (tiles_m * tiles_n, nsplit); tile rows m0 = tm * 128 (columns of A), cols n0 = tn * NT (columns of B)
+template <int NT>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_gram_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ B, int64_t ldb, int64_t n,
-               int ma, int mb, int NT, int tiles_n, int64_t rows_per_split, double* __restrict__ part, int* flag) {
+               int ma, int mb, int tiles_n, int64_t rows_per_split, double* __restrict__ part, int* flag) {
   extern __shared__ __align__(1024) uint8_t dyn[];
   __shared__ TcSmem sm;
   const int tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
@@ -210,39 +226,54 @@ tc_gram_kernel(const double* __restrict__ A, int64_t lda, const double* __restri
   const int64_t r_begin = (int64_t)blockIdx.y * rows_per_split;
   const int64_t r_end = min(n, r_begin + rows_per_split);
   const int nk = r_end > r_begin ? (int)ceil_div(r_end - r_begin, kBK) : 0;
-  const uint32_t a_bytes = (kM / 8) * kSBO, b_bytes = (uint32_t)(NT / 8) * kSBO;
-  const uint32_t ncols = (uint32_t)NT;
+  constexpr uint32_t a_bytes = (kM / 8) * kSBO, b_bytes = (uint32_t)(NT / 8) * kSBO;
+  constexpr uint32_t ncols = (uint32_t)NT;
   tc_setup(sm, ncols);
   const uint32_t tmem = sm.tmem_slot;
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   const int mm = lane >> 2, kk = lane & 3;        // position inside a core matrix (8 rows x 4 k)
-  auto stage = [&](int kb, uint8_t* a_tile, uint8_t* b_tile) {
-    const int64_t r0 = r_begin + (int64_t)kb * kBK;
-    // A tile: 128 rows (columns of A) x 32 k (rows of A); core matrix (g, c) covers rows 8g.., k 4c..
-    for (int cm = warp; cm < (kM / 8) * (kBK / 4); cm += kThreads / 32) {
+  Stage<NT> reg;
+  auto load = [&](int kb) {
+    const int64_t gr = r_begin + (int64_t)kb * kBK;
+#pragma unroll
+    for (int i = 0; i < Stage<NT>::kA; ++i) {
+      const int cm = warp + i * (kThreads / 32);
       const int g = cm / (kBK / 4), c = cm % (kBK / 4);
-      const int row = 8 * g + mm, k = 4 * c + kk;
-      const int64_t gr = r0 + k;
-      const int gc = m0 + row;
-      const double v = (gr < r_end && gc < ma) ? __ldg(A + gr + (int64_t)gc * lda) : 0.0;
-      *reinterpret_cast<float*>(a_tile + tile_off(row, k)) = to_tf32(v);
+      const int64_t r = gr + 4 * c + kk;
+      const int col = m0 + 8 * g + mm;
+      reg.a[i] = (r < r_end && col < ma) ? __ldg(A + r + (int64_t)col * lda) : 0.0;
     }
-    for (int cm = warp; cm < (NT / 8) * (kBK / 4); cm += kThreads / 32) {
+#pragma unroll
+    for (int i = 0; i < Stage<NT>::kB; ++i) {
+      const int cm = warp + i * (kThreads / 32);
       const int g = cm / (kBK / 4), c = cm % (kBK / 4);
-      const int row = 8 * g + mm, k = 4 * c + kk;
-      const int64_t gr = r0 + k;
-      const int gc = n0 + row;
-      const double v = (gr < r_end && gc < mb) ? __ldg(B + gr + (int64_t)gc * ldb) : 0.0;
-      *reinterpret_cast<float*>(b_tile + tile_off(row, k)) = to_tf32(v);
+      const int64_t r = gr + 4 * c + kk;
+      const int col = n0 + 8 * g + mm;
+      reg.b[i] = (r < r_end && col < mb) ? __ldg(B + r + (int64_t)col * ldb) : 0.0;
     }
   };
-  const bool ok = tc_mainloop(nk, dyn, a_bytes, b_bytes, sm, tmem, idesc_tf32(kM, NT), stage);
+  auto store = [&](uint8_t* a_tile, uint8_t* b_tile) {
+#pragma unroll
+    for (int i = 0; i < Stage<NT>::kA; ++i) {
+      const int cm = warp + i * (kThreads / 32);
+      const int g = cm / (kBK / 4), c = cm % (kBK / 4);
+      *reinterpret_cast<float*>(a_tile + tile_off(8 * g + mm, 4 * c + kk)) = to_tf32(reg.a[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < Stage<NT>::kB; ++i) {
+      const int cm = warp + i * (kThreads / 32);
+      const int g = cm / (kBK / 4), c = cm % (kBK / 4);
+      *reinterpret_cast<float*>(b_tile + tile_off(8 * g + mm, 4 * c + kk)) = to_tf32(reg.b[i]);
+    }
+  };
+  const bool ok = tc_mainloop(nk, dyn, a_bytes, b_bytes, sm, tmem, idesc_tf32(kM, NT), load, store);
   if (ok) {
     // epilogue: warp w reads lanes 32 (w % 4).., columns [h NT/2, (h+1) NT/2) with h = w / 4
     double* out = part + (int64_t)blockIdx.y * ma * mb;
     const int q = warp & 3, h = warp >> 2;
     const int row = 32 * q + lane;
     const int gi = m0 + row;
+#pragma unroll 1
     for (int c0 = h * (NT / 2); c0 < (h + 1) * (NT / 2); c0 += 16) {
       float v[16];
       if (nk > 0) tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
@@ -263,46 +294,61 @@ tc_gram_kernel(const double* __restrict__ A, int64_t lda, const double* __restri
 
 // ------------------------------------------------------------------------------------------ Y = Y - A G / Y = A G
 // grid (ceil(n / 128), ceil(p / NT)); A: n x m, G: m x p, Y: n x p
+template <int NT>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_update_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ G, int ldg, int64_t n, int m,
-                 int p, int NT, double* Y, int64_t ldy, int subtract, int* flag) {
+                 int p, double* Y, int64_t ldy, int subtract, int* flag) {
   extern __shared__ __align__(1024) uint8_t dyn[];
   __shared__ TcSmem sm;
   const int64_t r0 = (int64_t)blockIdx.x * kM;
   const int c0 = blockIdx.y * NT;
   const int nk = (int)ceil_div(m, kBK);
-  const uint32_t a_bytes = (kM / 8) * kSBO, b_bytes = (uint32_t)(NT / 8) * kSBO;
-  const uint32_t ncols = (uint32_t)NT;
+  constexpr uint32_t a_bytes = (kM / 8) * kSBO, b_bytes = (uint32_t)(NT / 8) * kSBO;
+  constexpr uint32_t ncols = (uint32_t)NT;
   tc_setup(sm, ncols);
   const uint32_t tmem = sm.tmem_slot;
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
-  auto stage = [&](int kb, uint8_t* a_tile, uint8_t* b_tile) {
+  const int ar = lane & 7, ak = lane >> 3;        // A: lanes run down the rows (coalesced in X)
+  const int bn = lane >> 2, bk = lane & 3;        // B: lanes run along k (contiguous in G)
+  Stage<NT> reg;
+  auto load = [&](int kb) {
     const int k0 = kb * kBK;
-    // A tile (rows of A x k): lanes run down the rows (coalesced), core matrix (g, c)
-    const int ar = lane & 7, ak = lane >> 3;
-    for (int cm = warp; cm < (kM / 8) * (kBK / 4); cm += kThreads / 32) {
+#pragma unroll
+    for (int i = 0; i < Stage<NT>::kA; ++i) {
+      const int cm = warp + i * (kThreads / 32);
       const int g = cm % (kM / 8), c = cm / (kM / 8);
-      const int row = 8 * g + ar, k = 4 * c + ak;
-      const int64_t gr = r0 + row;
-      const int gk = k0 + k;
-      const double v = (gr < n && gk < m) ? __ldg(A + gr + (int64_t)gk * lda) : 0.0;
-      *reinterpret_cast<float*>(a_tile + tile_off(row, k)) = to_tf32(v);
+      const int64_t gr = r0 + 8 * g + ar;
+      const int gk = k0 + 4 * c + ak;
+      reg.a[i] = (gr < n && gk < m) ? __ldg(A + gr + (int64_t)gk * lda) : 0.0;
     }
-    // B tile (columns of G x k): lanes run along k (contiguous in G)
-    const int bn = lane >> 2, bk = lane & 3;
-    for (int cm = warp; cm < (NT / 8) * (kBK / 4); cm += kThreads / 32) {
+#pragma unroll
+    for (int i = 0; i < Stage<NT>::kB; ++i) {
+      const int cm = warp + i * (kThreads / 32);
       const int g = cm / (kBK / 4), c = cm % (kBK / 4);
-      const int row = 8 * g + bn, k = 4 * c + bk;
-      const int gk = k0 + k;
-      const int gc = c0 + row;
-      const double v = (gk < m && gc < p) ? __ldg(G + gk + (int64_t)gc * ldg) : 0.0;
-      *reinterpret_cast<float*>(b_tile + tile_off(row, k)) = to_tf32(v);
+      const int gk = k0 + 4 * c + bk;
+      const int gc = c0 + 8 * g + bn;
+      reg.b[i] = (gk < m && gc < p) ? __ldg(G + gk + (int64_t)gc * ldg) : 0.0;
     }
   };
-  const bool ok = tc_mainloop(nk, dyn, a_bytes, b_bytes, sm, tmem, idesc_tf32(kM, NT), stage);
+  auto store = [&](uint8_t* a_tile, uint8_t* b_tile) {
+#pragma unroll
+    for (int i = 0; i < Stage<NT>::kA; ++i) {
+      const int cm = warp + i * (kThreads / 32);
+      const int g = cm % (kM / 8), c = cm / (kM / 8);
+      *reinterpret_cast<float*>(a_tile + tile_off(8 * g + ar, 4 * c + ak)) = to_tf32(reg.a[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < Stage<NT>::kB; ++i) {
+      const int cm = warp + i * (kThreads / 32);
+      const int g = cm / (kBK / 4), c = cm % (kBK / 4);
+      *reinterpret_cast<float*>(b_tile + tile_off(8 * g + bn, 4 * c + bk)) = to_tf32(reg.b[i]);
+    }
+  };
+  const bool ok = tc_mainloop(nk, dyn, a_bytes, b_bytes, sm, tmem, idesc_tf32(kM, NT), load, store);
   if (ok) {
     const int q = warp & 3, h = warp >> 2;
     const int64_t gr = r0 + 32 * q + lane;
+#pragma unroll 1
     for (int cc = h * (NT / 2); cc < (h + 1) * (NT / 2); cc += 16) {
       float v[16];
       if (nk > 0) tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)cc, v);
@@ -310,13 +356,16 @@ tc_update_kernel(const double* __restrict__ A, int64_t lda, const double* __rest
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = 0.f;
       if (gr < n) {
+        double y[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int gc = c0 + cc + i;
-          if (gc < p) {
-            double* y = Y + gr + (int64_t)gc * ldy;
-            *y = subtract ? (*y - (double)v[i]) : (double)v[i];
-          }
+          y[i] = (subtract && gc < p) ? Y[gr + (int64_t)gc * ldy] : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int gc = c0 + cc + i;
+          if (gc < p) Y[gr + (int64_t)gc * ldy] = subtract ? (y[i] - (double)v[i]) : (double)v[i];
         }
       }
     }
@@ -360,6 +409,30 @@ int sm_count() {
   return sms;
 }
 
+
+template <int NT>
+cudaError_t launch_gram(dim3 grid, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n, int ma,
+                        int mb, int tiles_n, int64_t rows, double* part, int* flag, cudaStream_t s) {
+  size_t smem = tc_smem_bytes(NT);
+  cudaError_t e = set_smem((const void*)tc_gram_kernel<NT>, smem, NT);
+  if (e != cudaSuccess) return e;
+  tc_gram_kernel<NT><<<grid, kThreads, smem, s>>>(A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int NT>
+cudaError_t launch_update(const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p, double* Y,
+                          int64_t ldy, bool subtract, int* flag, cudaStream_t s) {
+  size_t smem = tc_smem_bytes(NT);
+  cudaError_t e = set_smem((const void*)tc_update_kernel<NT>, smem, NT);
+  if (e != cudaSuccess) return e;
+  tc_update_kernel<NT><<<dim3((unsigned)ceil_div(n, kM), (unsigned)ceil_div(p, NT)), kThreads, smem, s>>>(
+      A, lda, G, ldg, n, m, p, Y, ldy, subtract ? 1 : 0, flag);
+  count_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t tc_gram(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n, int ma, int mb, double* C,
@@ -376,14 +449,16 @@ cudaError_t tc_gram(const double* A, int64_t lda, const double* B, int64_t ldb, 
   const int64_t cap_mem = (int64_t)(part_capacity / ((size_t)ma * mb));
   nsplit = std::min(nsplit, std::min(cap_traffic, std::min(cap_rows, cap_mem)));
   if (nsplit < 1) nsplit = 1;
-  int64_t rows = ceil_div(ceil_div(n, nsplit), kBK) * kBK;
+  const int64_t rows = ceil_div(ceil_div(n, nsplit), kBK) * kBK;
   const int nsp = (int)ceil_div(n, rows);
-  size_t smem = tc_smem_bytes(NT);
-  cudaError_t e = set_smem((const void*)tc_gram_kernel, smem, NT);
-  if (e != cudaSuccess) return e;
-  tc_gram_kernel<<<dim3(tiles, nsp), kThreads, smem, s>>>(A, lda, B, ldb, n, ma, mb, NT, tiles_n, rows, part, flag);
-  count_launch();
-  e = cudaGetLastError();
+  const dim3 grid(tiles, nsp);
+  cudaError_t e;
+  switch (NT) {
+    case 32: e = launch_gram<32>(grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag, s); break;
+    case 64: e = launch_gram<64>(grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag, s); break;
+    case 128: e = launch_gram<128>(grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag, s); break;
+    default: e = launch_gram<256>(grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag, s); break;
+  }
   if (e != cudaSuccess) return e;
   return gram_reduce_partials(part, nsp, ma, mb, C, ldc, symmetric, s);
 }
@@ -391,14 +466,12 @@ cudaError_t tc_gram(const double* A, int64_t lda, const double* B, int64_t ldb, 
 cudaError_t tc_update(const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p, double* Y,
                       int64_t ldy, bool subtract, int* flag, cudaStream_t s) {
   if (p <= 0 || n <= 0) return cudaSuccess;
-  const int NT = pick_nt(p);
-  size_t smem = tc_smem_bytes(NT);
-  cudaError_t e = set_smem((const void*)tc_update_kernel, smem, NT);
-  if (e != cudaSuccess) return e;
-  tc_update_kernel<<<dim3((unsigned)ceil_div(n, kM), (unsigned)ceil_div(p, NT)), kThreads, smem, s>>>(
-      A, lda, G, ldg, n, m, p, NT, Y, ldy, subtract ? 1 : 0, flag);
-  count_launch();
-  return cudaGetLastError();
+  switch (pick_nt(p)) {
+    case 32: return launch_update<32>(A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
+    case 64: return launch_update<64>(A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
+    case 128: return launch_update<128>(A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
+    default: return launch_update<256>(A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
+  }
 }
 
 }  // namespace ppcg
