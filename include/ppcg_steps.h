@@ -63,6 +63,13 @@ PPCG_API ppcg_status ppcg_block_update(ppcg_handle h, double* X, const double* W
 PPCG_API ppcg_status ppcg_residual(ppcg_handle h, const double* X, const double* HX, int64_t ld, int32_t m, const double* M,
                           const double* lam, double sigma, double* W, double* colnorm2);
 
+/* Adjoint of the solve with respect to the potential (Hellmann-Feynman): for E = sum_{i<k} lambda_i and
+ * unit-norm eigenvectors x_i of A = -Laplacian_h + diag(V), dE/dV_p = sum_{i<k} x_i(p)^2 (the density), valid
+ * when lambda_k < lambda_{k+1}. grad_V[p] = scale * sum_{c<k} X[p, c]^2 for X n x k (ld), as returned by
+ * ppcg_solve; scale is the upstream gradient of E. Device pointers; grad_V has n entries. */
+PPCG_API ppcg_status ppcg_energy_gradient(ppcg_handle h, const double* X, int64_t ld, int32_t k, double scale,
+                                          double* grad_V);
+
 /* Gram matrix C = A^T B without a handle and without allocating any device memory. The paper has no
  * counterpart: this entry point exists for callers that cannot allocate (a fixed device-memory budget, an
  * application memory pool that forbids cudaMalloc, no ppcg handle). A is n x ma (lda >= n), B is n x mb

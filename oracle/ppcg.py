@@ -294,6 +294,13 @@ def normalize_phase(X):
     return X
 
 
+def energy_gradient(X):
+    """dE/dV for E = sum of the k smallest eigenvalues of -Laplacian_h + diag(V): by the Hellmann-Feynman theorem
+    (d lambda_i / dV_p = |x_i(p)|^2 for a unit eigenvector x_i of a simple eigenvalue; for the sum over a set of
+    eigenvalues separated from the rest, the projector's diagonal), the density sum_{i<k} |x_i(p)|^2."""
+    return np.sum(np.abs(X) ** 2, axis=1)
+
+
 # --------------------------------------------------------------------------------------------------------
 # Algorithm 3
 # --------------------------------------------------------------------------------------------------------

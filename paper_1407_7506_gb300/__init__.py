@@ -26,7 +26,8 @@ PHASES = ("AX", "GEMM", "BlockRR", "CholQR", "RR", "Precond", "Lock", "Other")
 
 EXPORTS = ("ppcg_status_string", "ppcg_workspace_bytes", "ppcg_create", "ppcg_set_potential", "ppcg_solve",
            "ppcg_destroy", "ppcg_apply_operator", "ppcg_gram", "ppcg_project", "ppcg_cholqr2", "ppcg_dense_eigh",
-           "ppcg_block_coefficients", "ppcg_block_update", "ppcg_residual", "ppcg_gram_noalloc")
+           "ppcg_block_coefficients", "ppcg_block_update", "ppcg_residual", "ppcg_gram_noalloc",
+           "ppcg_energy_gradient")
 
 
 class ppcg_operator(ctypes.Structure):
@@ -89,6 +90,7 @@ def lib():
             "ppcg_block_update": (_i32, [_vp, _vp, _vp, _vp, _i64, _i32, _i32, _vp]),
             "ppcg_residual": (_i32, [_vp, _vp, _vp, _i64, _i32, _vp, _vp, _d, _vp, _vp]),
             "ppcg_gram_noalloc": (_i32, [_vp, _i64, _vp, _i64, _i64, _i32, _i32, _vp, _vp]),
+            "ppcg_energy_gradient": (_i32, [_vp, _vp, _i64, _i32, _d, _vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -173,9 +175,14 @@ def ppcg_residual(h, X, HX, ld, m, M, lam, sigma, W, colnorm2):
     _check(lib().ppcg_residual(h, X, HX, ld, m, M, lam, sigma, W, colnorm2), "ppcg_residual")
 
 
+def ppcg_energy_gradient(h, X, ld, k, scale, grad_V):
+    _check(lib().ppcg_energy_gradient(h, X, ld, k, scale, grad_V), "ppcg_energy_gradient")
+
+
 def ppcg_gram_noalloc(A, lda, B, ldb, n, ma, mb, C, stream=0):
     """C = A^T B without a handle and without device allocation (static scratch; ma * mb <= 2**20)."""
     _check(lib().ppcg_gram_noalloc(A, lda, B, ldb, n, ma, mb, C, stream), "ppcg_gram_noalloc")
 
 
 from .solver import Solver  # noqa: E402,F401
+from .autograd import smallest_eigsum  # noqa: E402,F401

@@ -777,4 +777,11 @@ ppcg_status ppcg_residual(ppcg_handle c, const double* X, const double* HX, int6
   return PPCG_OK;
 }
 
+ppcg_status ppcg_energy_gradient(ppcg_handle c, const double* X, int64_t ld, int32_t k, double scale,
+                                 double* grad_V) {
+  if (!c || !X || !grad_V || k < 1 || ld < c->n || !std::isfinite(scale)) return PPCG_ERR_ARG;
+  CK(density(X, ld, c->n, k, scale, grad_V, c->stream));
+  return PPCG_OK;
+}
+
 }  // extern "C"

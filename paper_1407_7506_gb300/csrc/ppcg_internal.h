@@ -83,6 +83,8 @@ cudaError_t gather_cols(const double* in, int64_t ldi, double* out, int64_t ldo,
                         cudaStream_t s);
 // Unit norm and largest-modulus entry (lowest index on ties) positive, in place on n x m.
 cudaError_t normalize_phase(double* X, int64_t ld, int64_t n, int m, double* scratch, cudaStream_t s);
+// rho[p] = scale * sum_{c < k} X[p, c]^2
+cudaError_t density(const double* X, int64_t ld, int64_t n, int k, double scale, double* rho, cudaStream_t s);
 // dg = 6 * inv_h2 + V
 cudaError_t make_diag(const double* V, double inv_h2, int64_t n, double* dg, cudaStream_t s);
 // count non-finite entries of v[0..m) into *bad (device int)

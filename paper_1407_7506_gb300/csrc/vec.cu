@@ -93,6 +93,26 @@ __global__ void __launch_bounds__(1024) phase_kernel(double* X, int64_t ld, int6
   for (int64_t r = threadIdx.x; r < n; r += blockDim.x) x[r] *= sc;
 }
 
+// rho[p] = scale * sum_{c < k} X[p, c]^2 : the Hellmann-Feynman gradient of the sum of the k Ritz values with
+// respect to the potential (one thread per grid point; every column read is coalesced across the warp)
+__global__ void __launch_bounds__(256)
+density_kernel(const double* __restrict__ X, int64_t ld, int64_t n, int k, double scale, double* __restrict__ rho) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int c = 0;
+    for (; c + 4 <= k; c += 4) {
+      const double a = __ldg(X + p + (int64_t)c * ld), b = __ldg(X + p + (int64_t)(c + 1) * ld);
+      const double d = __ldg(X + p + (int64_t)(c + 2) * ld), e = __ldg(X + p + (int64_t)(c + 3) * ld);
+      s0 = fma(a, a, s0); s1 = fma(b, b, s1); s2 = fma(d, d, s2); s3 = fma(e, e, s3);
+    }
+    for (; c < k; ++c) {
+      const double a = __ldg(X + p + (int64_t)c * ld);
+      s0 = fma(a, a, s0);
+    }
+    rho[p] = scale * ((s0 + s1) + (s2 + s3));
+  }
+}
+
 __global__ void make_diag_kernel(const double* __restrict__ V, double six_inv_h2, int64_t n, double* dg) {
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
     dg[r] = six_inv_h2 + V[r];
@@ -136,6 +156,14 @@ cudaError_t gather_cols(const double* in, int64_t ldi, double* out, int64_t ldo,
 cudaError_t normalize_phase(double* X, int64_t ld, int64_t n, int m, double* /*scratch*/, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
   phase_kernel<<<m, 1024, 0, s>>>(X, ld, n);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t density(const double* X, int64_t ld, int64_t n, int k, double scale, double* rho, cudaStream_t s) {
+  int64_t blocks = ceil_div(n, 256);
+  if (blocks > 8192) blocks = 8192;
+  density_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, ld, n, k, scale, rho);
   count_launch();
   return cudaGetLastError();
 }

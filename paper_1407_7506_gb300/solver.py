@@ -53,8 +53,8 @@ class Solver:
                                   self.workspace.data_ptr(), nbytes)
 
     def set_potential(self, V):
-        V = torch.as_tensor(V, dtype=torch.float64)
-        V = V if V.device.type == "cpu" else V.contiguous()
+        V = torch.as_tensor(V, dtype=torch.float64).contiguous()
+        self._V = V                      # keep alive across the (synchronous) copy
         ppcg_set_potential(self.handle, V.data_ptr())
 
     def solve(self, X0, tol=1e-8, out=None):

@@ -351,3 +351,28 @@ def test_planted_transposed_projection_is_caught():
     Y = rng.standard_normal((200, 7))
     bad = Y - X @ (Y.T @ X)                            # transposed Gram
     assert np.max(np.abs(X.T @ bad)) > 1e-3
+
+
+# ---------------------------------------------------------------- adjoint (Hellmann-Feynman gradient)
+def test_energy_gradient_matches_central_differences_of_dense_eigenvalues():
+    N, k, h = 6, 7, 1e-4
+    rng = _rng(61)
+    V = rng.random(N ** 3)
+    ev, U = np.linalg.eigh(oracle.assemble_H(V, N, 1.0))
+    assert ev[k] - ev[k - 1] > 1e-3                     # gap above lambda_k: E is differentiable
+    g = oracle.energy_gradient(U[:, :k])
+    np.testing.assert_allclose(np.sum(g), k, rtol=1e-13)     # sum_p dE/dV_p = k (unit vectors)
+    for p in rng.choice(N ** 3, 6, replace=False):
+        e = np.zeros(N ** 3)
+        e[p] = h
+        Ep = np.sum(np.linalg.eigvalsh(oracle.assemble_H(V + e, N, 1.0))[:k])
+        Em = np.sum(np.linalg.eigvalsh(oracle.assemble_H(V - e, N, 1.0))[:k])
+        assert abs((Ep - Em) / (2 * h) - g[p]) <= 1e-7 * max(abs(g[p]), k / N ** 3)
+
+
+def test_constant_potential_shift_moves_energy_by_k_c():
+    N, k, c = 6, 7, 0.37
+    V = _rng(62).random(N ** 3)
+    E0 = np.sum(np.linalg.eigvalsh(oracle.assemble_H(V, N, 1.0))[:k])
+    E1 = np.sum(np.linalg.eigvalsh(oracle.assemble_H(V + c, N, 1.0))[:k])
+    np.testing.assert_allclose(E1 - E0, k * c, rtol=1e-12)
