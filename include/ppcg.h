@@ -70,7 +70,9 @@ typedef struct {
   double* history;      /* [NULL] host array of 4 * history_cap doubles; entry i = {iteration, kind,
                            value, trace}: kind 0 = plain step (value = ||W||_F over the wanted columns),
                            kind 1 = Rayleigh-Ritz step (value = max_i r_i, trace = sum of the k Ritz values) */
-  int32_t reserved[6];
+  int32_t fp64_gemm;    /* [0] how the FP64 n x k GEMMs run: 0 = FP64 FMA pipe, 1 = FP64-accurate emulation on
+                           the BF16 tensor cores (error-free splitting into 8 digit slices, Ozaki scheme) */
+  int32_t reserved[5];
 } ppcg_options;
 
 /* Phases of the per-phase times, after the paper's profile categories (Tables Li318prof, Siprof) */

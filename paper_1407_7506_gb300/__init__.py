@@ -39,7 +39,7 @@ class ppcg_options(ctypes.Structure):
     _fields_ = [("maxiter", ctypes.c_int32), ("nbuf", ctypes.c_int32), ("no_lock", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("sigma_floor", ctypes.c_double), ("timing", ctypes.c_int32),
                 ("history_cap", ctypes.c_int32), ("history", ctypes.POINTER(ctypes.c_double)),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("fp64_gemm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class ppcg_stats(ctypes.Structure):

@@ -15,8 +15,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libppcg.so")
-SOURCES = ["api.cu", "stencil.cu", "gemm.cu", "vec.cu", "blockrr.cu", "dense.cu", "tcgemm.cu"]
-HEADERS = ["ppcg_internal.h", os.path.join("..", "..", "include", "ppcg.h"),
+SOURCES = ["api.cu", "stencil.cu", "gemm.cu", "vec.cu", "blockrr.cu", "dense.cu", "tcgemm.cu", "ozaki.cu"]
+HEADERS = ["ppcg_internal.h", "tc_util.cuh", os.path.join("..", "..", "include", "ppcg.h"),
            os.path.join("..", "..", "include", "ppcg_steps.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

@@ -54,6 +54,8 @@ struct ppcg_ctx {
   double t_ms[8] = {};
   int last_sweeps = 0;
   bool mixed = false;      // PPCG_MIXED_TF32: projections and the first CholQR Gram on tcgen05
+  bool ozaki = false;      // FP64 n x k GEMMs emulated on the BF16 tensor cores (error-free splitting)
+  int* ozexps = nullptr;   // exponent workspace of the emulated GEMMs
   int* tcflag = nullptr;   // timeout flag of the tensor-core kernels
 };
 
@@ -96,7 +98,7 @@ Sizes make_sizes(int64_t n, int kt, int q) {
 // Offsets of every region; returns the total byte count.
 struct Offsets {
   size_t V, dg, blk[7], G, M, C, Rinv, lam, norms, normpart, gpart, bpart, coef, cholws, jacws;
-  size_t iflag, icnt, jinfo, idx, bflags, bar;
+  size_t iflag, icnt, jinfo, idx, bflags, bar, ozexps;
   size_t total;
 };
 
@@ -126,6 +128,7 @@ Offsets layout(const Sizes& s) {
   o.idx = L.off(s.kt, 4);
   o.bflags = L.off(s.smax, 4);
   o.bar = L.off(barrier_words(), 4);
+  o.ozexps = L.off(oz_exp_elems(s.n, s.kt), 4);
   o.total = L.bytes + kAlign;
   return o;
 }
@@ -145,6 +148,7 @@ ppcg_status check_args(const ppcg_operator* op, int64_t n, int32_t k, int32_t sb
   if (sbsize < 1 || sbsize > kMaxSbsize || sbsize > kt) return PPCG_ERR_ARG;
   if (opt && (opt->maxiter < 0 || opt->sigma_floor < 0.0)) return PPCG_ERR_ARG;
   if (opt && opt->precision != PPCG_FP64 && opt->precision != PPCG_MIXED_TF32) return PPCG_ERR_UNSUPPORTED;
+  if (opt && (opt->fp64_gemm < 0 || opt->fp64_gemm > 1)) return PPCG_ERR_ARG;
   return PPCG_OK;
 }
 
@@ -200,10 +204,38 @@ ppcg_status apply_H(ppcg_ctx* c, const double* X, int64_t ldx, double* Y, int64_
   return PPCG_OK;
 }
 
+// FP64 Gram over the n grid rows: FP64 pipe, or the FP64-accurate tensor-core emulation when selected
 ppcg_status gram(ppcg_ctx* c, const double* A, int64_t lda, const double* B, int64_t ldb, int ma, int mb,
                  double* Cm, int ldc) {
   const bool sym = (A == B && lda == ldb && ma == mb);
-  CK(ppcg::gram(A, lda, B, ldb, c->n, ma, mb, Cm, ldc, sym, c->gpart, c->gpart_cap, c->stream));
+  if (c->ozaki)
+    CK(oz_gram(A, lda, B, ldb, c->n, ma, mb, Cm, ldc, sym, c->gpart, c->gpart_cap, c->ozexps, c->tcflag, c->stream));
+  else
+    CK(ppcg::gram(A, lda, B, ldb, c->n, ma, mb, Cm, ldc, sym, c->gpart, c->gpart_cap, c->stream));
+  return PPCG_OK;
+}
+
+// FP64 update Y = A G (Store) or Y = Y - A G (Sub) over the n grid rows; g_upper trims the FP64-pipe K loop
+ppcg_status update(ppcg_ctx* c, const double* A, int64_t lda, const double* G, int ldg, int m, int p, double* Y,
+                   int64_t ldy, Epi mode, bool g_upper) {
+  if (c->ozaki)
+    CK(oz_update(A, lda, G, ldg, c->n, m, p, Y, ldy, mode, c->ozexps, c->tcflag, c->stream));
+  else
+    CK(gemm_nn(A, lda, G, ldg, c->n, m, p, Y, ldy, nullptr, 0, mode, g_upper, nullptr, c->stream));
+  return PPCG_OK;
+}
+
+// Steps 20 / 8 fused: W = T (HX - X M) with column norms of HX - X M in norm_part
+ppcg_status residual_m(ppcg_ctx* c, const double* X, const double* HX, int64_t ld, int m, const double* Mm,
+                       const ResidualArgs& ra, double* W) {
+  if (c->ozaki) {
+    CK(cudaMemcpy2DAsync(W, ld * sizeof(double), HX, ld * sizeof(double), c->n * sizeof(double), m,
+                         cudaMemcpyDeviceToDevice, c->stream));
+    PS(update(c, X, ld, Mm, m, m, m, W, ld, Epi::Sub, false));
+    CK(precond_norms(W, ld, c->n, m, ra, c->stream));
+  } else {
+    CK(gemm_nn(X, ld, Mm, m, c->n, m, m, W, ld, HX, ld, Epi::Residual, false, &ra, c->stream));
+  }
   return PPCG_OK;
 }
 
@@ -225,7 +257,7 @@ ppcg_status project(ppcg_ctx* c, const double* X, int64_t ldx, int mx, double* Y
     return PPCG_OK;
   }
   PS(gram(c, X, ldx, Y, ldy, mx, my, c->G, mx));
-  CK(gemm_nn(X, ldx, c->G, mx, c->n, mx, my, Y, ldy, nullptr, 0, Epi::Sub, false, nullptr, c->stream));
+  PS(update(c, X, ldx, c->G, mx, mx, my, Y, ldy, Epi::Sub, false));
   return PPCG_OK;
 }
 
@@ -236,7 +268,7 @@ ppcg_status cholqr_pass(ppcg_ctx* c, const double* Xin, int64_t ldi, double* Xou
   if (lowprec) PS(gram_tc(c, Xin, ldi, Xin, ldi, m, m, c->G, m));
   else PS(gram(c, Xin, ldi, Xin, ldi, m, m, c->G, m));
   CK(chol_inv(c->G, m, shift, c->Rinv, c->cholws, c->iflag, c->bar, c->stream));
-  CK(gemm_nn(Xin, ldi, c->Rinv, m, c->n, m, m, Xout, ldo, nullptr, 0, Epi::Store, true, nullptr, c->stream));
+  PS(update(c, Xin, ldi, c->Rinv, m, m, m, Xout, ldo, Epi::Store, true));
   return PPCG_OK;
 }
 
@@ -369,7 +401,7 @@ ppcg_status rr_step(ppcg_ctx* c, SolveState& st, bool allow_compact, ppcg_stats*
     // coefficients R^{-1} Z (R^{-1} is upper triangular)
     CK(gemm_nn(c->Rinv, kt, c->C, kt, kt, kt, kt, c->G, kt, nullptr, 0, Epi::Store, false, nullptr, s));
   }
-  CK(gemm_nn(c->X, c->ld, c->G, kt, c->n, kt, kt, c->Xs, c->ld, nullptr, 0, Epi::Store, false, nullptr, s));
+  PS(update(c, c->X, c->ld, c->G, kt, kt, kt, c->Xs, c->ld, Epi::Store, false));
   swap(c->X, c->Xs);
   phase_mark(c, PPCG_T_AX);
   PS(apply_H(c, c->X, c->ld, c->HX, c->ld, kt));
@@ -547,6 +579,8 @@ ppcg_status ppcg_create(const ppcg_operator* op, int64_t n, int32_t k, int32_t s
   c->bar = reinterpret_cast<unsigned*>(b + o.bar);
   c->tcflag = c->icnt + 2;
   c->mixed = (c->opt.precision == PPCG_MIXED_TF32);
+  c->ozaki = (c->opt.fp64_gemm == 1);
+  c->ozexps = reinterpret_cast<int*>(b + o.ozexps);
   c->lam_h.assign(c->kt, 0.0);
   c->nrm_h.assign(c->kt, 0.0);
   ppcg_status st = ppcg_set_potential(c, op->V);
@@ -644,7 +678,7 @@ ppcg_status ppcg_solve(ppcg_handle c, const double* X0, double tol, double* lamb
       phase_mark(c, PPCG_T_GEMM);
       PS(gram(c, Xa, ld, HXa, ld, ka, ka, c->M, ka));
       ResidualArgs ra = resid_args(c, st.sigma);
-      CK(gemm_nn(Xa, ld, c->M, ka, n, ka, ka, c->W, ld, HXa, ld, Epi::Residual, false, &ra, s));
+      PS(residual_m(c, Xa, HXa, ld, ka, c->M, ra, c->W));
       CK(reduce_colnorms(c->normpart, norm_row_tiles(n), ka, c->norms, s));
       CK(cudaMemcpyAsync(c->nrm_h.data(), c->norms, sizeof(double) * ka, cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
@@ -771,7 +805,7 @@ ppcg_status ppcg_residual(ppcg_handle c, const double* X, const double* HX, int6
   if (!c || !X || !HX || !W || !colnorm2 || m < 1 || m > c->kt || ld < c->n) return PPCG_ERR_ARG;
   if (!M && !lam) return PPCG_ERR_ARG;
   ResidualArgs ra = resid_args(c, sigma);
-  if (M) CK(gemm_nn(X, ld, M, m, c->n, m, m, W, ld, HX, ld, Epi::Residual, false, &ra, c->stream));
+  if (M) PS(residual_m(c, X, HX, ld, m, M, ra, W));
   else CK(residual_diag(X, HX, ld, c->n, m, lam, ra, W, c->stream));
   CK(reduce_colnorms(c->normpart, norm_row_tiles(c->n), m, colnorm2, c->stream));
   return PPCG_OK;

@@ -1,0 +1,532 @@
+// FP64-accurate tall-skinny GEMMs on the BF16 tensor cores by error-free splitting (the Ozaki scheme: Ozaki,
+// Ogita, Oishi, Rump, "Error-free transformations of matrix multiplication by using fast routines of matrix
+// multiplication and its applications", Numer. Algorithms 2012), written for tcgen05.
+//
+// Every FP64 element x of a column (Gram) or row (update) whose magnitudes are below 2^E is rounded to the
+// integer T = round(x 2^(54 - E)) and written as 8 balanced base-128 digits d_j in [-63, 64]:
+//   x = sum_{j<8} d_j 2^(E - 5 - 7 j)  (to 2^-55 relative to the column maximum).
+// A digit is exact in BF16 and a digit product is at most 2^12, so the 36 digit-pair products with
+// j + l = g (g = 0..7) can share one FP32 TMEM accumulator: over a chunk of 256 summed terms each group stays an
+// integer below 2^23 and the tensor-core accumulation is exact. After every chunk the 8 group accumulators are
+// folded, with weights 2^(-7 g), into a double-float (FP32 pair) register accumulator; one FP64 scale by
+// 2^(E_a + E_b - 10) per element produces the result. The error is that of the 55-bit digits plus the ~2^-48
+// relative rounding of the double-float sum, below the rounding of an FP64 GEMM of these lengths.
+//
+// Tiles: M = 128 rows (TMEM lanes) x N = 64 columns; the 8 group accumulators fill the 512 TMEM columns of an SM.
+// Operand tiles are staged by the threads (coalesced FP64 loads, integer digit extraction, BF16 stores into the
+// K-major canonical layout, 8 digit planes per operand, 2 stages); one thread issues the 72 MMAs of a stage.
+#include "ppcg_internal.h"
+#include "tc_util.cuh"
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+namespace ppcg {
+
+cudaError_t gram_reduce_partials(const double* part, int nsplit, int ma, int mb, double* C, int ldc, bool symmetric,
+                                 cudaStream_t s);
+
+namespace {
+
+using namespace tc;
+
+constexpr int kM = 128;
+constexpr int kN = 64;
+constexpr int kDig = 8;                   // digits per element
+constexpr int kGroups = 8;                // g = j + l <= 7
+constexpr int kBK = 32;                   // K per stage (2 MMAs of K = 16)
+constexpr int kChunk = 256;               // exact-accumulation chunk (8 * 256 * 2^12 = 2^23)
+constexpr int kThreads = 256;
+constexpr uint32_t kLBO = 128;            // bytes between core matrices along K (8 bf16)
+constexpr uint32_t kSBO = (kBK / 8) * 128;  // bytes between 8-row groups
+constexpr uint32_t kAPlane = (kM / 8) * kSBO;   // 8 KB
+constexpr uint32_t kBPlane = (kN / 8) * kSBO;   // 4 KB
+constexpr uint32_t kStageBytes = kDig * (kAPlane + kBPlane);   // 96 KB
+constexpr int kNoExp = -2000;             // exponent of an all-zero line
+
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t tile_off(int row, int k) {
+  return (uint32_t)(row >> 3) * kSBO + (uint32_t)(row & 7) * 16u + (uint32_t)(k >> 3) * kLBO + (uint32_t)(k & 7) * 2u;
+}
+
+// 8 balanced base-128 digits of round(x 2^(54 - E)), most significant first; integer operations only
+__device__ __forceinline__ void digits(double x, int E, int (&d)[kDig]) {
+  const long long bits = __double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  long long T = 0;
+  if (ex != 0 && E > kNoExp) {
+    const long long m = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+    const int sh = ex - 1021 - E;                 // x = m 2^(ex - 1075); T = m 2^(ex - 1075 + 54 - E)
+    if (sh >= 0) T = m << (sh < 2 ? sh : 2);      // |x| < 2^E gives sh <= 1
+    else if (sh > -63) T = (m + (1LL << (-sh - 1))) >> (-sh);
+    if (bits < 0) T = -T;
+  }
+#pragma unroll
+  for (int j = kDig - 1; j >= 0; --j) {
+    int r = (int)(T & 127);
+    r = r > 64 ? r - 128 : r;
+    d[j] = r;
+    T = (T - r) >> 7;
+  }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(int lo, int hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn((float)lo, (float)hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ double pow2(int e) {   // 2^e for e in the normal range
+  e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+// ------------------------------------------------------------------------------------------ exponent bounds
+// E[c] = smallest e with max_r |M[r, c]| < 2^e (kNoExp for a zero column); one warp per column
+__global__ void col_exp_kernel(const double* __restrict__ M, int64_t ld, int64_t rows, int cols, int* __restrict__ E) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x & 31;
+  if (warp >= cols) return;
+  const double* col = M + (int64_t)warp * ld;
+  double mx = 0.0;
+  for (int64_t r = lane; r < rows; r += 32) mx = fmax(mx, fabs(__ldg(col + r)));
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if (lane == 0) {
+    const long long b = __double_as_longlong(mx);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    E[warp] = (mx == 0.0 || ex == 0) ? kNoExp : ex - 1022;   // mx in [2^(ex-1023), 2^(ex-1022))
+  }
+}
+
+// E[r] = smallest e with max_c |M[r, c]| < 2^e; one thread per row
+__global__ void row_exp_kernel(const double* __restrict__ M, int64_t ld, int64_t rows, int cols, int* __restrict__ E) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+    double mx = 0.0;
+    for (int c = 0; c < cols; ++c) mx = fmax(mx, fabs(__ldg(M + r + (int64_t)c * ld)));
+    const long long b = __double_as_longlong(mx);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    E[r] = (mx == 0.0 || ex == 0) ? kNoExp : ex - 1022;
+  }
+}
+
+// ------------------------------------------------------------------------------------------ shared machinery
+struct OzSmem {
+  uint64_t mbar[2];
+  uint32_t tmem_slot;
+  int ok;
+  int Ea[kM];
+  int Eb[kN];
+};
+
+__device__ void oz_setup(OzSmem& sm) {
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&sm.mbar[0]), 1);
+    mbar_init(smem_u32(&sm.mbar[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (threadIdx.x / 32 == 0) tmem_alloc(smem_u32(&sm.tmem_slot), 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+}
+
+__device__ void oz_teardown(OzSmem& sm, uint32_t tmem, bool ok, int gstage, int* flag) {
+  if (!ok && threadIdx.x == 0) {
+    atomicOr(flag, kFlagTimeout);
+    if (gstage > 0) mbar_wait(smem_u32(&sm.mbar[(gstage - 1) & 1]), (uint32_t)(((gstage - 1) >> 1) & 1));
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x / 32 == 0) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// the 72 MMAs of one stage: for g = j + l, both K halves of the stage
+__device__ __forceinline__ void issue_stage(uint32_t tmem, uint8_t* stage, bool first_stage_of_chunk) {
+  const uint32_t a0 = smem_u32(stage), b0 = a0 + kDig * kAPlane;
+  constexpr uint32_t idesc = idesc_bf16(kM, kN);
+#pragma unroll
+  for (int g = 0; g < kGroups; ++g) {
+#pragma unroll
+    for (int j = 0; j <= g; ++j) {
+      const int l = g - j;
+#pragma unroll
+      for (int ks = 0; ks < kBK / 16; ++ks) {
+        const uint32_t acc = (first_stage_of_chunk && j == 0 && ks == 0) ? 0u : 1u;
+        mma_bf16(tmem + (uint32_t)(g * kN), smem_desc_nosw(a0 + j * kAPlane + ks * 2 * kLBO, kLBO, kSBO),
+                 smem_desc_nosw(b0 + l * kBPlane + ks * 2 * kLBO, kLBO, kSBO), idesc, acc);
+      }
+    }
+  }
+}
+
+// fold the 8 group accumulators of this warp's 32 lanes x 32 columns into (hi, lo)
+__device__ __forceinline__ void fold_groups(uint32_t tmem, int q, int h, float (&hi)[32], float (&lo)[32]) {
+#pragma unroll 1
+  for (int g = kGroups - 1; g >= 0; --g) {
+    float v[32];
+    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(g * kN + 32 * h), v);
+    const float w = __int_as_float((127 - 7 * g) << 23);   // 2^(-7 g), exact
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const float x = v[i] * w;
+      const float s = hi[i] + x;
+      const float bb = s - hi[i];
+      lo[i] += (hi[i] - (s - bb)) + (x - bb);
+      hi[i] = s;
+    }
+  }
+}
+
+// per-thread staging registers: A core matrices (8 rows x 8 k, 2 elements per lane) and B core matrices
+constexpr int kACm = (kM / 8) * (kBK / 8) / (kThreads / 32);   // 8
+constexpr int kBCm = (kN / 8) * (kBK / 8) / (kThreads / 32);   // 4
+struct Regs {
+  double a[kACm][2];
+  double b[kBCm][2];
+};
+
+// ------------------------------------------------------------------------------------------ C = A^T B partials
+// grid (tiles_m * tiles_n, nsplit); A: n x ma, B: n x mb; Ea/Eb column exponent bounds over all n rows
+__global__ void __launch_bounds__(kThreads, 1)
+oz_gram_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ B, int64_t ldb, int64_t n,
+               int ma, int mb, int tiles_n, int64_t rows_per_split, const int* __restrict__ Ea,
+               const int* __restrict__ Eb, double* __restrict__ part, int symmetric, int* flag) {
+  extern __shared__ __align__(1024) uint8_t dyn[];
+  __shared__ OzSmem sm;
+  const int tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
+  const int m0 = tm * kM, n0 = tn * kN;
+  if (symmetric && n0 + kN <= m0) return;        // entirely below the diagonal: the reduce reads only i <= j
+  const int64_t r_begin = (int64_t)blockIdx.y * rows_per_split;
+  const int64_t r_end = min(n, r_begin + rows_per_split);
+  for (int i = threadIdx.x; i < kM; i += kThreads) sm.Ea[i] = (m0 + i < ma) ? Ea[m0 + i] : kNoExp;
+  for (int i = threadIdx.x; i < kN; i += kThreads) sm.Eb[i] = (n0 + i < mb) ? Eb[n0 + i] : kNoExp;
+  oz_setup(sm);
+  const uint32_t tmem = sm.tmem_slot;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  const int rr = lane >> 2, kp = lane & 3;       // inside a core matrix: row rr, k = 2 kp, 2 kp + 1
+  const int q = warp & 3, h = warp >> 2;
+  float hi[32], lo[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) { hi[i] = 0.f; lo[i] = 0.f; }
+  Regs reg;
+  auto load = [&](int64_t k0, int64_t kend) {
+#pragma unroll
+    for (int i = 0; i < kACm; ++i) {
+      const int cm = warp + i * (kThreads / 32);
+      const int g8 = cm / (kBK / 8), c8 = cm % (kBK / 8);
+      const int col = m0 + 8 * g8 + rr;
+      const int64_t r = k0 + 8 * c8 + 2 * kp;
+      const double* p = A + r + (int64_t)col * lda;
+      reg.a[i][0] = (col < ma && r < kend) ? __ldg(p) : 0.0;
+      reg.a[i][1] = (col < ma && r + 1 < kend) ? __ldg(p + 1) : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < kBCm; ++i) {
+      const int cm = warp + i * (kThreads / 32);
+      const int g8 = cm / (kBK / 8), c8 = cm % (kBK / 8);
+      const int col = n0 + 8 * g8 + rr;
+      const int64_t r = k0 + 8 * c8 + 2 * kp;
+      const double* p = B + r + (int64_t)col * ldb;
+      reg.b[i][0] = (col < mb && r < kend) ? __ldg(p) : 0.0;
+      reg.b[i][1] = (col < mb && r + 1 < kend) ? __ldg(p + 1) : 0.0;
+    }
+  };
+  auto store = [&](uint8_t* stage) {
+#pragma unroll
+    for (int i = 0; i < kACm; ++i) {
+      const int cm = warp + i * (kThreads / 32);
+      const int g8 = cm / (kBK / 8), c8 = cm % (kBK / 8);
+      const int E = sm.Ea[8 * g8 + rr];
+      int d0[kDig], d1[kDig];
+      digits(reg.a[i][0], E, d0);
+      digits(reg.a[i][1], E, d1);
+      const uint32_t off = tile_off(8 * g8 + rr, 8 * c8 + 2 * kp);
+#pragma unroll
+      for (int j = 0; j < kDig; ++j)
+        *reinterpret_cast<uint32_t*>(stage + j * kAPlane + off) = pack_bf16x2(d0[j], d1[j]);
+    }
+    uint8_t* bst = stage + kDig * kAPlane;
+#pragma unroll
+    for (int i = 0; i < kBCm; ++i) {
+      const int cm = warp + i * (kThreads / 32);
+      const int g8 = cm / (kBK / 8), c8 = cm % (kBK / 8);
+      const int E = sm.Eb[8 * g8 + rr];
+      int d0[kDig], d1[kDig];
+      digits(reg.b[i][0], E, d0);
+      digits(reg.b[i][1], E, d1);
+      const uint32_t off = tile_off(8 * g8 + rr, 8 * c8 + 2 * kp);
+#pragma unroll
+      for (int j = 0; j < kDig; ++j)
+        *reinterpret_cast<uint32_t*>(bst + j * kBPlane + off) = pack_bf16x2(d0[j], d1[j]);
+    }
+  };
+  int gstage = 0;
+  bool ok = true;
+  for (int64_t c0 = r_begin; c0 < r_end && ok; c0 += kChunk) {
+    const int64_t cend = min(r_end, c0 + kChunk);
+    const int nk = (int)ceil_div(cend - c0, kBK);
+    load(c0, cend);
+    for (int kb = 0; kb < nk; ++kb, ++gstage) {
+      const int s = gstage & 1;
+      uint8_t* stage = dyn + s * kStageBytes;
+      if (gstage >= 2) {
+        if (threadIdx.x == 0) sm.ok = mbar_wait(smem_u32(&sm.mbar[s]), (uint32_t)(((gstage - 2) >> 1) & 1)) ? 1 : 0;
+        __syncthreads();
+        if (!sm.ok) { ok = false; break; }
+      }
+      store(stage);
+      if (kb + 1 < nk) load(c0 + (int64_t)(kb + 1) * kBK, cend);
+      fence_async_smem();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        tc_fence_after();
+        issue_stage(tmem, stage, kb == 0);
+        mma_commit(smem_u32(&sm.mbar[s]));
+      }
+    }
+    if (!ok) break;
+    if (threadIdx.x == 0) sm.ok = mbar_wait(smem_u32(&sm.mbar[(gstage - 1) & 1]), (uint32_t)(((gstage - 1) >> 1) & 1)) ? 1 : 0;
+    __syncthreads();
+    if (!sm.ok) { ok = false; break; }
+    tc_fence_after();
+    fold_groups(tmem, q, h, hi, lo);
+    tc_fence_before();
+    __syncthreads();
+  }
+  if (ok) {
+    double* out = part + (int64_t)blockIdx.y * ma * mb;
+    const int ri = 32 * q + lane;
+    const int gi = m0 + ri;
+    if (gi < ma) {
+      const int Ei = sm.Ea[ri];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int cj = 32 * h + i;
+        const int gj = n0 + cj;
+        if (gj >= mb) continue;
+        const int Ej = sm.Eb[cj];
+        const double v = (Ei == kNoExp || Ej == kNoExp) ? 0.0 : ((double)hi[i] + (double)lo[i]) * pow2(Ei + Ej - 10);
+        out[gi + (int64_t)gj * ma] = v;
+      }
+    }
+  }
+  oz_teardown(sm, tmem, ok, gstage, flag);
+}
+
+// ------------------------------------------------------------------------------------------ Y = Y -/+ A G
+// grid (ceil(n / 128), ceil(p / 64)); A: n x m, G: m x p; Er: row exponents of A, Fc: column exponents of G
+__global__ void __launch_bounds__(kThreads, 1)
+oz_update_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ G, int ldg, int64_t n, int m,
+                 int p, double* Y, int64_t ldy, int mode, const int* __restrict__ Er, const int* __restrict__ Fc,
+                 int* flag) {
+  extern __shared__ __align__(1024) uint8_t dyn[];
+  __shared__ OzSmem sm;
+  const int64_t r0 = (int64_t)blockIdx.x * kM;
+  const int c0 = blockIdx.y * kN;
+  for (int i = threadIdx.x; i < kM; i += kThreads) sm.Ea[i] = (r0 + i < n) ? Er[r0 + i] : kNoExp;
+  for (int i = threadIdx.x; i < kN; i += kThreads) sm.Eb[i] = (c0 + i < p) ? Fc[c0 + i] : kNoExp;
+  oz_setup(sm);
+  const uint32_t tmem = sm.tmem_slot;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  const int rr = lane >> 2, kp = lane & 3;
+  const int q = warp & 3, h = warp >> 2;
+  float hi[32], lo[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) { hi[i] = 0.f; lo[i] = 0.f; }
+  Regs reg;
+  // A tile: rows of A x k (columns of A); B tile: columns of G x k (rows of G)
+  auto load = [&](int k0, int kend) {
+#pragma unroll
+    for (int i = 0; i < kACm; ++i) {
+      const int cm = warp + i * (kThreads / 32);
+      const int g8 = cm / (kBK / 8), c8 = cm % (kBK / 8);
+      const int64_t row = r0 + 8 * g8 + rr;
+      const int k = k0 + 8 * c8 + 2 * kp;
+      reg.a[i][0] = (row < n && k < kend) ? __ldg(A + row + (int64_t)k * lda) : 0.0;
+      reg.a[i][1] = (row < n && k + 1 < kend) ? __ldg(A + row + (int64_t)(k + 1) * lda) : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < kBCm; ++i) {
+      const int cm = warp + i * (kThreads / 32);
+      const int g8 = cm / (kBK / 8), c8 = cm % (kBK / 8);
+      const int col = c0 + 8 * g8 + rr;
+      const int k = k0 + 8 * c8 + 2 * kp;
+      const double* pp = G + k + (int64_t)col * ldg;
+      reg.b[i][0] = (col < p && k < kend) ? __ldg(pp) : 0.0;
+      reg.b[i][1] = (col < p && k + 1 < kend) ? __ldg(pp + 1) : 0.0;
+    }
+  };
+  auto store = [&](uint8_t* stage) {
+#pragma unroll
+    for (int i = 0; i < kACm; ++i) {
+      const int cm = warp + i * (kThreads / 32);
+      const int g8 = cm / (kBK / 8), c8 = cm % (kBK / 8);
+      const int E = sm.Ea[8 * g8 + rr];
+      int d0[kDig], d1[kDig];
+      digits(reg.a[i][0], E, d0);
+      digits(reg.a[i][1], E, d1);
+      const uint32_t off = tile_off(8 * g8 + rr, 8 * c8 + 2 * kp);
+#pragma unroll
+      for (int j = 0; j < kDig; ++j)
+        *reinterpret_cast<uint32_t*>(stage + j * kAPlane + off) = pack_bf16x2(d0[j], d1[j]);
+    }
+    uint8_t* bst = stage + kDig * kAPlane;
+#pragma unroll
+    for (int i = 0; i < kBCm; ++i) {
+      const int cm = warp + i * (kThreads / 32);
+      const int g8 = cm / (kBK / 8), c8 = cm % (kBK / 8);
+      const int E = sm.Eb[8 * g8 + rr];
+      int d0[kDig], d1[kDig];
+      digits(reg.b[i][0], E, d0);
+      digits(reg.b[i][1], E, d1);
+      const uint32_t off = tile_off(8 * g8 + rr, 8 * c8 + 2 * kp);
+#pragma unroll
+      for (int j = 0; j < kDig; ++j)
+        *reinterpret_cast<uint32_t*>(bst + j * kBPlane + off) = pack_bf16x2(d0[j], d1[j]);
+    }
+  };
+  int gstage = 0;
+  bool ok = true;
+  for (int k0 = 0; k0 < m && ok; k0 += kChunk) {
+    const int kend = min(m, k0 + kChunk);
+    const int nk = (int)ceil_div(kend - k0, kBK);
+    load(k0, kend);
+    for (int kb = 0; kb < nk; ++kb, ++gstage) {
+      const int s = gstage & 1;
+      uint8_t* stage = dyn + s * kStageBytes;
+      if (gstage >= 2) {
+        if (threadIdx.x == 0) sm.ok = mbar_wait(smem_u32(&sm.mbar[s]), (uint32_t)(((gstage - 2) >> 1) & 1)) ? 1 : 0;
+        __syncthreads();
+        if (!sm.ok) { ok = false; break; }
+      }
+      store(stage);
+      if (kb + 1 < nk) load(k0 + (kb + 1) * kBK, kend);
+      fence_async_smem();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        tc_fence_after();
+        issue_stage(tmem, stage, kb == 0);
+        mma_commit(smem_u32(&sm.mbar[s]));
+      }
+    }
+    if (!ok) break;
+    if (threadIdx.x == 0) sm.ok = mbar_wait(smem_u32(&sm.mbar[(gstage - 1) & 1]), (uint32_t)(((gstage - 1) >> 1) & 1)) ? 1 : 0;
+    __syncthreads();
+    if (!sm.ok) { ok = false; break; }
+    tc_fence_after();
+    fold_groups(tmem, q, h, hi, lo);
+    tc_fence_before();
+    __syncthreads();
+  }
+  if (ok) {
+    const int ri = 32 * q + lane;
+    const int64_t gr = r0 + ri;
+    if (gr < n) {
+      const int Ei = sm.Ea[ri];
+      double yv[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int gc = c0 + 32 * h + i;
+        yv[i] = (mode != (int)Epi::Store && gc < p) ? Y[gr + (int64_t)gc * ldy] : 0.0;
+      }
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int cj = 32 * h + i;
+        const int gc = c0 + cj;
+        if (gc >= p) continue;
+        const int Ej = sm.Eb[cj];
+        const double v = (Ei == kNoExp || Ej == kNoExp) ? 0.0 : ((double)hi[i] + (double)lo[i]) * pow2(Ei + Ej - 10);
+        Y[gr + (int64_t)gc * ldy] = mode == (int)Epi::Store ? v : yv[i] - v;
+      }
+    }
+  }
+  oz_teardown(sm, tmem, ok, gstage, flag);
+}
+
+size_t oz_smem() { return 2 * (size_t)kStageBytes + 1024; }
+
+int sm_count() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+// one CTA per SM: the kernels allocate all 512 TMEM columns
+cudaError_t prep(const void* fn) {
+  const size_t smem = oz_smem();
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  return per_sm <= 1 ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
+}  // namespace
+
+size_t oz_exp_elems(int64_t n, int cols) { return (size_t)(n > cols ? n : cols) + (size_t)cols + 64; }
+
+cudaError_t oz_gram(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n, int ma, int mb, double* C,
+                    int ldc, bool symmetric, double* part, size_t part_capacity, int* exps, int* flag,
+                    cudaStream_t s) {
+  if (ma <= 0 || mb <= 0) return cudaSuccess;
+  if ((size_t)ma * mb > part_capacity) return cudaErrorInvalidValue;
+  int* Ea = exps;
+  int* Eb = exps + ma;
+  col_exp_kernel<<<(unsigned)ceil_div(ma, 8), 256, 0, s>>>(A, lda, n, ma, Ea);
+  count_launch();
+  if (!(symmetric && A == B)) {
+    col_exp_kernel<<<(unsigned)ceil_div(mb, 8), 256, 0, s>>>(B, ldb, n, mb, Eb);
+    count_launch();
+  } else {
+    Eb = Ea;
+  }
+  cudaError_t e = prep((const void*)oz_gram_kernel);
+  if (e != cudaSuccess) return e;
+  const int tiles_m = (int)ceil_div(ma, kM), tiles_n = (int)ceil_div(mb, kN);
+  const int tiles = tiles_m * tiles_n;
+  int64_t nsplit = ceil_div(sm_count(), tiles);
+  const int64_t cap_rows = ceil_div(n, kChunk);
+  const int64_t cap_mem = (int64_t)(part_capacity / ((size_t)ma * mb));
+  nsplit = std::max<int64_t>(1, std::min(nsplit, std::min(cap_rows, cap_mem)));
+  const int64_t rows = ceil_div(ceil_div(n, nsplit), kChunk) * kChunk;
+  const int nsp = (int)ceil_div(n, rows);
+  oz_gram_kernel<<<dim3(tiles, nsp), kThreads, oz_smem(), s>>>(A, lda, B, ldb, n, ma, mb, tiles_n, rows, Ea, Eb,
+                                                                  part, symmetric ? 1 : 0, flag);
+  count_launch();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return gram_reduce_partials(part, nsp, ma, mb, C, ldc, symmetric, s);
+}
+
+cudaError_t oz_update(const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p, double* Y,
+                      int64_t ldy, Epi mode, int* exps, int* flag, cudaStream_t s) {
+  if (p <= 0 || n <= 0) return cudaSuccess;
+  int* Er = exps;
+  int* Fc = exps + n;
+  int64_t blocks = ceil_div(n, 256);
+  row_exp_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(A, lda, n, m, Er);
+  count_launch();
+  col_exp_kernel<<<(unsigned)ceil_div(p, 8), 256, 0, s>>>(G, ldg, m, p, Fc);
+  count_launch();
+  cudaError_t e = prep((const void*)oz_update_kernel);
+  if (e != cudaSuccess) return e;
+  oz_update_kernel<<<dim3((unsigned)ceil_div(n, kM), (unsigned)ceil_div(p, kN)), kThreads, oz_smem(), s>>>(
+      A, lda, G, ldg, n, m, p, Y, ldy, (int)mode, Er, Fc, flag);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace ppcg

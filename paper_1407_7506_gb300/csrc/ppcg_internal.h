@@ -72,10 +72,22 @@ cudaError_t tc_gram(const double* A, int64_t lda, const double* B, int64_t ldb, 
 cudaError_t tc_update(const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p, double* Y,
                       int64_t ldy, bool subtract, int* flag, cudaStream_t s);
 
+// ---------------------------------------------------------------------------------------------- Ozaki (FP64)
+// FP64-accurate versions of gram / gemm_nn (Store or Sub) on the BF16 tensor cores by error-free splitting.
+// exps: int workspace of oz_exp_elems(n, max columns) entries.
+size_t oz_exp_elems(int64_t n, int cols);
+cudaError_t oz_gram(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n, int ma, int mb, double* C,
+                    int ldc, bool symmetric, double* part, size_t part_capacity, int* exps, int* flag,
+                    cudaStream_t s);
+cudaError_t oz_update(const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p, double* Y,
+                      int64_t ldy, Epi mode, int* exps, int* flag, cudaStream_t s);
+
 // ---------------------------------------------------------------------------------------------- vectors
 // R = HX - X diag(lam); W = T R; norm_part per row tile.
 cudaError_t residual_diag(const double* X, const double* HX, int64_t ld, int64_t n, int m, const double* lam,
                           const ResidualArgs& ra, double* W, cudaStream_t s);
+// W (holding R) <- T R in place; norm_part per row tile gets the column sums of R^2
+cudaError_t precond_norms(double* W, int64_t ld, int64_t n, int m, const ResidualArgs& ra, cudaStream_t s);
 // out[c] = sum over row tiles of norm_part[t * m + c]
 cudaError_t reduce_colnorms(const double* norm_part, int64_t tiles, int m, double* out, cudaStream_t s);
 // out[:, j] = idx[j] >= 0 ? in[:, idx[j]] : 0 for j < m

@@ -38,6 +38,33 @@ residual_diag_kernel(const double* __restrict__ X, const double* __restrict__ HX
   }
 }
 
+// W holds R: norm_part per row tile gets the column sums of R^2, then W = T R in place
+__global__ void __launch_bounds__(256)
+precond_norms_kernel(double* __restrict__ W, int64_t ld, int64_t n, int m, const double* __restrict__ dg,
+                     double sigma, double delta, double* __restrict__ norm_part) {
+  const int r_loc = threadIdx.x % kRows;
+  const int c_loc = threadIdx.x / kRows;
+  const int64_t r = (int64_t)blockIdx.x * kRows + r_loc;
+  const int c = blockIdx.y * 4 + c_loc;
+  double sq = 0.0;
+  if (r < n && c < m) {
+    const int64_t o = (int64_t)c * ld + r;
+    const double rr = W[o];
+    sq = rr * rr;
+    W[o] = rr / fmax(dg[r] - sigma, delta);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
+  __shared__ double red[8];
+  const int warp = threadIdx.x / 32;
+  if ((threadIdx.x & 31) == 0) red[warp] = sq;
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    const int cc = blockIdx.y * 4 + threadIdx.x;
+    if (cc < m) norm_part[(int64_t)blockIdx.x * m + cc] = red[2 * threadIdx.x] + red[2 * threadIdx.x + 1];
+  }
+}
+
 __global__ void reduce_colnorms_kernel(const double* __restrict__ part, int64_t tiles, int m, double* out) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= m) return;
@@ -132,6 +159,14 @@ cudaError_t residual_diag(const double* X, const double* HX, int64_t ld, int64_t
   if (m <= 0) return cudaSuccess;
   dim3 grid((unsigned)norm_row_tiles(n), (unsigned)ceil_div(m, 4));
   residual_diag_kernel<<<grid, 256, 0, s>>>(X, HX, ld, n, m, lam, ra.dg, ra.sigma, ra.delta, W, ra.norm_part);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t precond_norms(double* W, int64_t ld, int64_t n, int m, const ResidualArgs& ra, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  dim3 grid((unsigned)norm_row_tiles(n), (unsigned)ceil_div(m, 4));
+  precond_norms_kernel<<<grid, 256, 0, s>>>(W, ld, n, m, ra.dg, ra.sigma, ra.delta, ra.norm_part);
   count_launch();
   return cudaGetLastError();
 }

@@ -37,13 +37,14 @@ def ptr(t):
 class Handle:
     """A ppcg handle used for the step-level entry points."""
 
-    def __init__(self, V, N, kt, sbsize, nbuf=0, h=1.0, precision=0):
+    def __init__(self, V, N, kt, sbsize, nbuf=0, h=1.0, precision=0, fp64_gemm=0):
         self.V = torch.as_tensor(np.asarray(V, dtype=np.float64)).cuda()
         self.N, self.n = N, N ** 3
         op = pk.ppcg_operator(N, N, N, h, self.V.data_ptr(), (ctypes.c_double * 3)(0, 0, 0), 0)
         opt = pk.ppcg_options()
         opt.nbuf = nbuf
         opt.precision = precision
+        opt.fp64_gemm = fp64_gemm
         nbytes = pk.ppcg_workspace_bytes(op, self.n, kt - nbuf, sbsize, opt)
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         self.h = pk.ppcg_create(op, self.n, kt - nbuf, sbsize, 5, opt, torch.cuda.current_stream().cuda_stream,

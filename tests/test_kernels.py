@@ -326,3 +326,77 @@ def test_project_tensor_core_tf32(N, mx, my):
     assert np.all(np.abs(Z - ref) <= bound)
     # the projection still removes span(X) up to the TF32 level
     assert np.max(np.abs(X.T @ Z)) < 50 * U_TF32 * np.max(np.abs(Y)) * np.sqrt(n)
+
+
+# ------------------------------------------------------------------------------------- FP64 emulation (Ozaki)
+@pytest.mark.parametrize("N,ma,mb,sym,spread", [(5, 37, 61, False, 0), (10, 70, 130, False, 30),
+                                                (16, 256, 256, False, 0), (16, 130, 130, True, 20),
+                                                (16, 200, 33, False, 5), (10, 1, 1, False, 0)])
+def test_gram_fp64_emulation(N, ma, mb, sym, spread):
+    # columns scaled by 2^[-spread, spread], one zero column: the per-column exponents must follow
+    n = N ** 3
+    rng = _rng(ma * 31 + mb)
+    A = rng.standard_normal((n, ma)) * np.exp2(rng.integers(-spread, spread + 1, ma))[None, :]
+    if ma > 2:
+        A[:, 1] = 0.0
+    B = A if sym else rng.standard_normal((n, mb)) * np.exp2(rng.integers(-spread, spread + 1, mb))[None, :]
+    with Handle(np.zeros(n), N, kt=max(ma, mb), sbsize=1, fp64_gemm=1) as H:
+        Ad = dev(A)
+        Bd = Ad if sym else dev(B)
+        Cd = torch.empty((mb, ma), dtype=torch.float64, device="cuda")
+        pk.ppcg_gram(H.h, ptr(Ad), n, ptr(Bd), n, ma, mb, ptr(Cd))
+        C = host(Cd)
+    ref = A.T @ B
+    bound = 2 * n * EPS * (np.abs(A).T @ np.abs(B))          # the FP64 GEMM bar of test_gram
+    assert np.all(np.abs(C - ref) <= bound + 1e-300), np.max(np.abs(C - ref) / (bound + 1e-300))
+    if sym:
+        np.testing.assert_array_equal(C, C.T)
+
+
+@pytest.mark.parametrize("N,mx,my", [(11, 40, 25), (16, 256, 256), (13, 70, 130)])
+def test_project_fp64_emulation(N, mx, my):
+    n = N ** 3
+    rng = _rng(mx + 3 * my)
+    X = oracle.cholqr2(rng.standard_normal((n, mx)))[0]
+    Y = rng.standard_normal((n, my))
+    with Handle(np.zeros(n), N, kt=max(mx, my), sbsize=1, fp64_gemm=1) as H:
+        Xd, Yd = dev(X), dev(Y)
+        pk.ppcg_project(H.h, ptr(Xd), n, mx, ptr(Yd), n, my)
+        Z = host(Yd)
+    np.testing.assert_allclose(Z, oracle.project(Y, X), rtol=0, atol=1e-12 * np.max(np.abs(Y)))
+    assert np.max(np.abs(X.T @ Z)) < 1e-12
+
+
+@pytest.mark.parametrize("N,m,cond", [(10, 33, 1e3), (16, 129, 1e2)])
+def test_cholqr2_fp64_emulation(N, m, cond):
+    n = N ** 3
+    rng = _rng(m + 1)
+    U = oracle.cholqr2(rng.standard_normal((n, m)))[0]
+    Vm = oracle.cholqr2(rng.standard_normal((m, m)))[0]
+    X = U @ np.diag(np.logspace(0, np.log10(cond), m)) @ Vm.T
+    with Handle(np.zeros(n), N, kt=m, sbsize=1, fp64_gemm=1) as H:
+        Xd = dev(X)
+        assert pk.ppcg_cholqr2(H.h, ptr(Xd), n, m) == 0
+        Q = host(Xd)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(m), atol=1e-12)
+    np.testing.assert_allclose(Q, oracle.cholqr2(X)[0], rtol=0, atol=1e-13 * cond)
+
+
+def test_residual_fp64_emulation():
+    N, m = 10, 21
+    n = N ** 3
+    rng = _rng(12)
+    V = rng.uniform(-3, 1, n)
+    X = oracle.cholqr2(rng.standard_normal((n, m)))[0]
+    HX = oracle.apply_H(V, N, 1.0, X)
+    M = X.T @ HX
+    R = oracle.residual(X, HX, M)
+    ref_W = oracle.precondition(R, V, N, 1.0, -1.5)
+    with Handle(V, N, kt=m, sbsize=1, fp64_gemm=1) as H:
+        Xd, HXd, Md = dev(X), dev(HX), dev(M)
+        Wd = torch.empty_like(Xd)
+        nd = torch.empty(m, dtype=torch.float64, device="cuda")
+        pk.ppcg_residual(H.h, ptr(Xd), ptr(HXd), n, m, ptr(Md), None, -1.5, ptr(Wd), ptr(nd))
+        W, nrm = host(Wd), nd.cpu().numpy()
+    np.testing.assert_allclose(W, ref_W, rtol=0, atol=1e-12 * np.max(np.abs(ref_W)))
+    np.testing.assert_allclose(nrm, np.sum(R * R, axis=0), rtol=1e-10)

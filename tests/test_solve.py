@@ -25,9 +25,10 @@ def _gpu():
     need_gpu()
 
 
-def _gpu_solve(V, N, k, q, rr, X0, tol=1e-8, nbuf=0, lock=True, maxiter=3000, history=0, precision="fp64"):
+def _gpu_solve(V, N, k, q, rr, X0, tol=1e-8, nbuf=0, lock=True, maxiter=3000, history=0, precision="fp64",
+               fp64_gemm="fma"):
     s = pk.Solver(V, N, k, q, rr_period=rr, nbuf=nbuf, lock=lock, maxiter=maxiter, history=history,
-                  precision=precision)
+                  precision=precision, fp64_gemm=fp64_gemm)
     try:
         lam, X, res, st = s.solve(X0, tol)
         return lam, X.cpu().numpy().T.copy(), res, st
@@ -134,6 +135,19 @@ def test_mixed_form_config1_against_dense_golden():
     lam, X, res, st = _gpu_solve(V, w.N, w.k, w.sbsize, w.rr_period, X0, tol=w.tol, maxiter=5000, precision="mixed")
     assert st["converged"] == 1, st
     assert np.all(_rel(lam, gold) <= LAM_TOL_MIXED), np.max(_rel(lam, gold))
+    _check_pairs(V, w.N, lam, X, w.tol)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fp64_emulation_solve_config1(precision):
+    # every FP64 n x k GEMM on the tensor cores (error-free splitting): the FP64-form bars still hold
+    w = wl.CONFIGS[1]
+    V, X0 = wl.make_inputs(w)
+    gold = np.loadtxt(os.path.join(GOLDEN, "config1_dense_eigs.txt"))[:w.k]
+    lam, X, res, st = _gpu_solve(V, w.N, w.k, w.sbsize, w.rr_period, X0, tol=w.tol, maxiter=5000,
+                                 precision=precision, fp64_gemm="ozaki")
+    assert st["converged"] == 1, st
+    assert np.all(_rel(lam, gold) <= (LAM_TOL if precision == "fp64" else LAM_TOL_MIXED)), np.max(_rel(lam, gold))
     _check_pairs(V, w.N, lam, X, w.tol)
 
 
