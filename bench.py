@@ -187,8 +187,8 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=3, help="oracle iterations in the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--no-emulation", action="store_true")
+    ap.add_argument("--forms", default="fp64,mixed,fp64_ozaki,mixed_ozaki",
+                    help="forms to time; the first is the headline value (fp64, mixed, fp64_ozaki, mixed_ozaki)")
     args = ap.parse_args()
     w = wl.CONFIGS[int(args.workload)]
     if args.impl == "reference":
@@ -258,14 +258,18 @@ def main():
                 "phase_ms": {k_: round(v_, 2) for k_, v_ in pst["t_phase_ms"].items()},
                 "jacobi_sweeps_max": pst["jacobi_sweeps_max"]}
 
+    forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     clk = ClockSampler(local)
-    fp64 = run_form("fp64", clk)
-    mixed = None if args.no_mixed else run_form("mixed_tf32", ClockSampler(local))
-    emu = {}
-    if not args.no_emulation:
-        emu["fp64"] = run_form("fp64", ClockSampler(local), fp64_gemm="ozaki")
-        if not args.no_mixed:
-            emu["mixed"] = run_form("mixed_tf32", ClockSampler(local), fp64_gemm="ozaki")
+    first = forms[0]
+    spec = {"fp64": ("fp64", "fma"), "mixed": ("mixed_tf32", "fma"), "fp64_ozaki": ("fp64", "ozaki"),
+            "mixed_ozaki": ("mixed_tf32", "ozaki")}
+    results = {}
+    for f in forms:
+        prec, gm = spec[f]
+        results[f] = run_form(prec, clk if f == first else ClockSampler(local), fp64_gemm=gm)
+    fp64 = results[first]
+    mixed = results.get("mixed")
+    emu = {k.split("_")[0]: v for k, v in results.items() if k.endswith("_ozaki")}
     ms_per_step = fp64["ms_per_step"]
     iters = fp64["iters"] * args.steps
     launches = fp64["launches"]
@@ -275,7 +279,7 @@ def main():
     roof = roofline(pk, probe, w, dev, stream)
     probe.close()
     roof_mixed = None
-    if mixed is not None:
+    if mixed is not None or "mixed_ozaki" in results:
         probe = pk.Solver(V_d, w.N, w.k, w.sbsize, rr_period=w.rr_period, maxiter=1, device=dev, stream=stream,
                           precision="mixed_tf32")
         roof_mixed = roofline_tc(pk, probe, w, dev, stream)
@@ -291,7 +295,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "n": w.n, "k": w.k, "sbsize": w.sbsize, "rr_period": w.rr_period,
-                   "tol": w.tol, "form": "fp64", "potential": f"{w.n_wells} Gaussian wells + U[0,0.1) noise",
+                   "tol": w.tol, "form": first, "potential": f"{w.n_wells} Gaussian wells + U[0,0.1) noise",
                    "l2": f"no flush: working set {7 * w.n * w.k * 8 / 2**20:.0f} MiB > {L2_BYTES // 2**20} MiB L2"},
         "iters": fp64["iters"], "iters_per_s": fp64["iters_per_s"], "wall_s_per_step": fp64["wall_s_per_step"],
         "parity": parity, "roofline": roof, "phase_ms": phases, "jacobi_sweeps_max": fp64["jacobi_sweeps_max"],
