@@ -1,7 +1,7 @@
 // Dense k x k kernels of Algorithm 3 (the ScaLAPACK part of Section 6):
 //   chol_inv     R^{-1} for the Cholesky factor of the Gram X^T X = R^T R (CholQR, Section 5.4, steps 18-19):
-//                blocked right-looking Cholesky on 32 x 32 tiles, then the inverse of L = R^T by tile
-//                diagonals; one cooperative persistent kernel, tile tasks spread over the CTAs.
+//                blocked right-looking Cholesky on 32 x 32 tiles with the inverse of L = R^T formed in the
+//                same sweep; one cooperative persistent kernel, quarter-tile tasks spread over the CTAs.
 //   jacobi_eigh  eigen-decomposition of the projected matrix of the Rayleigh-Ritz step (steps 23-24,
 //                Section 5.5): parallel cyclic Jacobi with round-robin pairing. In every round each 2 x 2 block
 //                of A is rotated from both sides independently (ping-pong buffers), each CTA recomputing the
@@ -19,7 +19,7 @@ namespace ppcg {
 namespace {
 
 constexpr int TB = 32;
-constexpr long long kSpinLimit = 1LL << 25;   // polls of ~50-100 ns: a wait longer than ~2-3 s is an error
+constexpr long long kSpinLimit = 1LL << 22;   // polls of ~0.3-1 us: a wait longer than ~1-4 s is an error
 
 // GPU-scope memory operations. (A volatile load is a relaxed load at system scope; on a CPU-coherent
 // Grace-Blackwell node that scope is far more expensive than the GPU scope these barriers need.)
@@ -33,50 +33,53 @@ __device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
   asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v) {
-  unsigned old;
-  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
-}
-__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void red_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 
-// Software grid barrier for cooperative launches (all CTAs co-resident). bar[0] counts arrivals, bar[1] is the
-// generation, which every CTA also tracks locally in `gen` (one increment per barrier), so arriving needs a single
-// atomic round trip. The wait is bounded: after kSpinLimit polls the CTA sets kFlagTimeout and every CTA returns
-// false.
+// Software grid barrier for cooperative launches (all CTAs co-resident). bar[0] counts arrivals over the whole
+// launch and is never reset, so barrier number g is passed once it reaches g * nblocks: arriving is one
+// fire-and-forget release add and waiting is polling with acquire loads (no return trip on arrival, no release
+// store by a last arriver). Every CTA tracks g locally in `gen`. The wait is bounded: after kSpinLimit polls the
+// CTA sets kFlagTimeout and every CTA returns false.
 __device__ bool grid_sync(unsigned* bar, unsigned nblocks, int* flag, unsigned& gen) {
   __shared__ int ok;
+  gen += 1u;
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned g = gen;
+    const unsigned target = gen * nblocks;
     __threadfence();                                   // publish this CTA's writes at GPU scope
-    const unsigned arrived = atom_add_acq_rel_gpu(bar, 1u);
+    red_release_gpu(bar, 1u);
     int good = 1;
-    if (arrived == nblocks - 1) {
-      bar[0] = 0u;                                     // ordered before the release below
-      st_release_gpu(bar + 1, g + 1u);
-    } else {
-      long long spins = 0;
-      while (ld_acquire_gpu(bar + 1) == g) {
-        if (++spins > kSpinLimit || (ld_relaxed_gpu(flag) & kFlagTimeout)) {
-          atomicOr(flag, kFlagTimeout);
-          good = 0;
-          break;
-        }
+    long long spins = 0;
+    while ((int)(ld_acquire_gpu(bar) - target) < 0) {
+      if ((++spins & 31) == 0 && (spins > kSpinLimit || (ld_relaxed_gpu(flag) & kFlagTimeout))) {
+        atomicOr(flag, kFlagTimeout);
+        good = 0;
+        break;
       }
     }
     __threadfence();
     if (ld_relaxed_gpu(flag) & kFlagTimeout) good = 0;
     ok = good;
   }
-  gen += 1u;
   __syncthreads();
   return ok != 0;
 }
 
 // ------------------------------------------------------------------------------------------- Cholesky
+// Blocked right-looking Cholesky of the padded matrix A = [G + shift I, 0; 0, I] = L L^T on 32 x 32 tiles, with
+// the inverse Y = L^{-1} formed in the same sweep by blocked forward substitution on an identity right-hand side
+// B: at step kk, Y_kk,: = L_kk^{-1} B_kk,: and B_i,: -= L_ik Y_kk,: for i > kk. Each step is two phases separated
+// by grid barriers:
+//   P (panel)    L_ik = A_ik L_kk^{-T} (i > kk) into a panel buffer, and Y_kk,j = L_kk^{-1} B_kk,j (j <= kk);
+//                every CTA with a task factors the diagonal tile A_kk itself, so no barrier separates the
+//                factorization of A_kk from its use;
+//   U (update)   A_ij -= L_ik L_jk^T (kk < j <= i) and B_ij -= L_ik Y_kk,j (i > kk, j <= kk).
+// Tasks are quarter tiles (32 rows x 8 columns, one output per thread). The diagonal tile is factored as
+// L1 D L1^T by Gaussian elimination that applies the same row operations to an identity (B1 = L1^{-1}), then
+// L_kk^{-1} = D^{-1/2} B1; one block barrier per column, with the next pivot's reciprocal formed by the thread that
+// finished that pivot.
 __device__ void load_tile(const double* M, int ld, int ti, int tj, double (*s)[TB + 1]) {
   for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
     const int r = e % TB, c = e / TB;
@@ -84,22 +87,55 @@ __device__ void load_tile(const double* M, int ld, int ti, int tj, double (*s)[T
   }
 }
 
-__device__ void store_tile(double* M, int ld, int ti, int tj, double (*s)[TB + 1]) {
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    const int r = e % TB, c = e / TB;
-    M[(int64_t)(ti * TB + r) + (int64_t)(tj * TB + c) * ld] = s[r][c];
+__device__ __forceinline__ void tile_pivot(double (*a)[TB + 1], double* sinv, int c, double g0, int* flag) {
+  double d = a[c][c];
+  if (!(d > 0.0 && d >= kCholPivotTol * kCholPivotTol * g0)) {
+    atomicOr(flag, kFlagCholBreakdown);
+    if (!(d > 0.0)) { d = 1.0; a[c][c] = 1.0; }
   }
+  sinv[c] = __drcp_rn(d);
+}
+
+// a: the symmetric diagonal tile (lower triangle used, overwritten); dinv receives L_kk^{-1} (lower triangular).
+__device__ void factor_tile(double (*a)[TB + 1], double (*dinv)[TB + 1], double* sinv, const double* diag0,
+                            int* flag) {
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
+  for (int e = t; e < TB * TB; e += blockDim.x) dinv[e % TB][e / TB] = (e % TB == e / TB) ? 1.0 : 0.0;
+  if (t == 0) tile_pivot(a, sinv, 0, __ldcg(diag0), flag);
+  __syncthreads();
+  for (int c = 0; c < TB; ++c) {
+    const double ic = sinv[c];
+    for (int r = c + 1 + w; r < TB; r += nw) {
+      const double l = a[r][c] * ic;                 // multiplier of row c in row r
+      const int j = lane;
+      if (j <= r) {
+        if (j > c) a[r][j] = fma(-l, a[j][c], a[r][j]);
+        else       dinv[r][j] = fma(-l, dinv[c][j], dinv[r][j]);
+      }
+    }
+    if (w == 0 && lane == c + 1) tile_pivot(a, sinv, c + 1, __ldcg(diag0 + c + 1), flag);
+    __syncthreads();
+  }
+  if (t < TB) sinv[t] = rsqrt(a[t][t]);              // D^{-1/2}
+  __syncthreads();
+  for (int e = t; e < TB * TB; e += blockDim.x) {
+    const int r = e % TB, j = e / TB;
+    dinv[r][j] = (j <= r) ? dinv[r][j] * sinv[r] : 0.0;
+  }
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(256)
 chol_inv_kernel(const double* __restrict__ G, int m, int mp, double shift, double* __restrict__ Rinv,
-                double* Lw, double* Linv, double* Dinv, double* diag0, int* flag, unsigned* bar) {
+                double* Lw, double* Linv, double* Lp, double* diag0, int* flag, unsigned* bar) {
   const int T = mp / TB;
   const unsigned nb = gridDim.x;
   const int t = threadIdx.x;
+  const int rr = t % TB, cq = t / TB;                // quarter-tile coordinates: row, column within the quarter
   unsigned gen = 0;
   __shared__ double s1[TB][TB + 1], s2[TB][TB + 1], s3[TB][TB + 1];
-  // fill the padded matrix [G + shift I, 0; 0, I]; only the lower triangle is used
+  __shared__ double sinv[TB];
+  // A = [G + shift I, 0; 0, I] (lower tiles are used), B = 0 below the diagonal tiles
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + t; e < (int64_t)mp * mp; e += (int64_t)nb * blockDim.x) {
     const int i = (int)(e % mp), j = (int)(e / mp);
     double v;
@@ -115,124 +151,81 @@ chol_inv_kernel(const double* __restrict__ G, int m, int mp, double shift, doubl
   }
   if (!grid_sync(bar, nb, flag, gen)) return;
   for (int kk = 0; kk < T; ++kk) {
-    if (blockIdx.x == 0) {
+    // ---- P: factor A_kk (per CTA), panel L_ik = A_ik Dinv^T into Lp, Y_kk,j = Dinv B_kk,j
+    const int np = 4 * T;
+    if ((int)blockIdx.x < np) {
       load_tile(Lw, mp, kk, kk, s1);
       __syncthreads();
-      for (int c = 0; c < TB; ++c) {
-        if (t == 0) {
-          const double a = s1[c][c];
-          const double g0 = __ldcg(diag0 + kk * TB + c);
-          double piv = a > 0.0 ? sqrt(a) : 0.0;
-          if (!(piv >= kCholPivotTol * sqrt(g0))) {
-            atomicOr(flag, kFlagCholBreakdown);
-            if (!(piv > 0.0)) piv = 1.0;
+      factor_tile(s1, s2, sinv, diag0 + kk * TB, flag);      // s2 = Dinv
+      for (int task = blockIdx.x; task < np; task += nb) {
+        const int q = task & 3, u = task >> 2;
+        const int c = q * 8 + cq;                            // column within the tile
+        if (kk + 1 + u < T) {
+          const int i = kk + 1 + u;
+          load_tile(Lw, mp, i, kk, s3);
+          __syncthreads();
+          double v = 0.0;
+          for (int l = 0; l <= c; ++l) v = fma(s3[rr][l], s2[c][l], v);
+          Lp[(int64_t)i * TB + rr + (int64_t)c * mp] = v;
+          __syncthreads();
+        } else {
+          const int j = u - (T - kk - 1);                    // 0..kk
+          double* Yt = Linv + (int64_t)kk * TB + (int64_t)j * TB * mp;
+          double v;
+          if (j == kk) {
+            v = s2[rr][c];
+          } else {
+            s3[rr][cq] = __ldcg(Yt + rr + (int64_t)c * mp);  // B_kk,j column c
+            __syncthreads();
+            v = 0.0;
+            for (int l = 0; l <= rr; ++l) v = fma(s2[rr][l], s3[l][cq], v);
+            __syncthreads();
           }
-          s1[c][c] = piv;
-        }
-        __syncthreads();
-        if (t > c && t < TB) s1[t][c] /= s1[c][c];
-        __syncthreads();
-        for (int e = t; e < TB * TB; e += blockDim.x) {
-          const int r = e % TB, j = e / TB;
-          if (j > c && r >= j) s1[r][j] -= s1[r][c] * s1[j][c];
-        }
-        __syncthreads();
-      }
-      // inverse of the lower-triangular tile (column per thread)
-      if (t < TB) {
-        const int c = t;
-        for (int i = 0; i < TB; ++i) s2[i][c] = 0.0;
-        s2[c][c] = 1.0 / s1[c][c];
-        for (int i = c + 1; i < TB; ++i) {
-          double v = 0.0;
-          for (int l = c; l < i; ++l) v += s1[i][l] * s2[l][c];
-          s2[i][c] = -v / s1[i][i];
+          Yt[rr + (int64_t)c * mp] = v;
         }
       }
-      __syncthreads();
-      store_tile(Lw, mp, kk, kk, s1);
-      store_tile(Dinv + (int64_t)kk * TB * TB, TB, 0, 0, s2);
     }
     if (!grid_sync(bar, nb, flag, gen)) return;
-    // panel: L_ik = A_ik Dinv_kk^T
-    for (int i = kk + 1 + blockIdx.x; i < T; i += nb) {
-      load_tile(Lw, mp, i, kk, s1);
-      load_tile(Dinv + (int64_t)kk * TB * TB, TB, 0, 0, s2);
-      __syncthreads();
-      for (int e = t; e < TB * TB; e += blockDim.x) {
-        const int r = e % TB, c = e / TB;
-        double v = 0.0;
-        for (int l = 0; l <= c; ++l) v += s1[r][l] * s2[c][l];
-        s3[r][c] = v;
-      }
-      __syncthreads();
-      store_tile(Lw, mp, i, kk, s3);
-      __syncthreads();
-    }
-    if (!grid_sync(bar, nb, flag, gen)) return;
-    // trailing update: A_ij -= L_ik L_jk^T, kk < j <= i
+    if (kk == T - 1) break;
+    // ---- U: A_ij -= L_ik L_jk^T (kk < j <= i), B_ij -= L_ik Y_kk,j (i > kk, j <= kk)
     const int R = T - kk - 1;
-    const int ntasks = R * (R + 1) / 2;
-    for (int task = blockIdx.x; task < ntasks; task += nb) {
-      int a = 0;
-      while ((a + 1) * (a + 2) / 2 <= task) ++a;
-      const int b = task - a * (a + 1) / 2;
-      const int i = kk + 1 + a, j = kk + 1 + b;
-      load_tile(Lw, mp, i, kk, s1);
-      load_tile(Lw, mp, j, kk, s2);
-      load_tile(Lw, mp, i, j, s3);
-      __syncthreads();
-      for (int e = t; e < TB * TB; e += blockDim.x) {
-        const int r = e % TB, c = e / TB;
-        double v = s3[r][c];
-        for (int l = 0; l < TB; ++l) v -= s1[r][l] * s2[c][l];
-        s3[r][c] = v;
+    const int na = 4 * (R * (R + 1) / 2), nbt = 4 * R * (kk + 1);
+    for (int task = blockIdx.x; task < na + nbt; task += nb) {
+      const int q = task & 3;
+      const int c = q * 8 + cq;
+      int i, j;
+      bool is_a;
+      if (task < na) {
+        const int tt = task >> 2;
+        int x = 0;
+        while ((x + 1) * (x + 2) / 2 <= tt) ++x;
+        i = kk + 1 + x;
+        j = kk + 1 + (tt - x * (x + 1) / 2);
+        is_a = true;
+      } else {
+        const int tt = (task - na) >> 2;
+        i = kk + 1 + tt % R;
+        j = tt / R;
+        is_a = false;
       }
-      __syncthreads();
-      store_tile(Lw, mp, i, j, s3);
-      __syncthreads();
-    }
-    if (!grid_sync(bar, nb, flag, gen)) return;
-  }
-  // L^{-1}: diagonal tiles are Dinv; tile (i, j), j < i: -Dinv_i * sum_{l=j}^{i-1} L_il Linv_lj
-  for (int i = blockIdx.x; i < T; i += nb) {
-    load_tile(Dinv + (int64_t)i * TB * TB, TB, 0, 0, s1);
-    __syncthreads();
-    store_tile(Linv, mp, i, i, s1);
-    __syncthreads();
-  }
-  if (!grid_sync(bar, nb, flag, gen)) return;
-  for (int d = 1; d < T; ++d) {
-    for (int i = d + blockIdx.x; i < T; i += nb) {
-      const int j = i - d;
-      double acc[4] = {0.0, 0.0, 0.0, 0.0};
-      for (int l = j; l < i; ++l) {
-        load_tile(Lw, mp, i, l, s1);
-        load_tile(Linv, mp, l, j, s2);
-        __syncthreads();
-        for (int u = 0; u < 4; ++u) {
-          const int e = t + u * blockDim.x;
-          const int r = e % TB, c = e / TB;
-          double v = 0.0;
-          for (int x = 0; x < TB; ++x) v += s1[r][x] * s2[x][c];
-          acc[u] += v;
+      // s1 = L_ik (panel), s3[:, 0:8] = the 8 needed columns of L_jk^T or Y_kk,j
+      for (int e = t; e < TB * TB; e += blockDim.x) s1[e % TB][e / TB] = __ldcg(Lp + (int64_t)i * TB + e % TB + (int64_t)(e / TB) * mp);
+      if (is_a) {
+        for (int e = t; e < TB * 8; e += blockDim.x) {
+          const int l = e % TB, cc = e / TB;                 // s3[l][cc] = L_jk[q*8+cc][l]
+          s3[l][cc] = __ldcg(Lp + (int64_t)j * TB + q * 8 + cc + (int64_t)l * mp);
         }
-        __syncthreads();
-      }
-      for (int u = 0; u < 4; ++u) {
-        const int e = t + u * blockDim.x;
-        s2[e % TB][e / TB] = acc[u];
-      }
-      load_tile(Dinv + (int64_t)i * TB * TB, TB, 0, 0, s1);
-      __syncthreads();
-      for (int e = t; e < TB * TB; e += blockDim.x) {
-        const int r = e % TB, c = e / TB;
-        double v = 0.0;
-        for (int x = 0; x <= r; ++x) v += s1[r][x] * s2[x][c];
-        s3[r][c] = -v;
+      } else {
+        for (int e = t; e < TB * 8; e += blockDim.x) {
+          const int l = e % TB, cc = e / TB;                 // s3[l][cc] = Y_kk,j[l][q*8+cc]
+          s3[l][cc] = __ldcg(Linv + (int64_t)kk * TB + l + (int64_t)(j * TB + q * 8 + cc) * mp);
+        }
       }
       __syncthreads();
-      store_tile(Linv, mp, i, j, s3);
+      double v = 0.0;
+      for (int l = 0; l < TB; ++l) v = fma(s1[rr][l], s3[l][cq], v);
+      double* dst = (is_a ? Lw : Linv) + (int64_t)i * TB + rr + (int64_t)(j * TB + c) * mp;
+      *dst = __ldcg(dst) - v;
       __syncthreads();
     }
     if (!grid_sync(bar, nb, flag, gen)) return;
@@ -250,18 +243,33 @@ chol_inv_kernel(const double* __restrict__ G, int m, int mp, double shift, doubl
 // the next round's pairing; the round writes its output directly at the shifted slots, so every 2 x 2 block load
 // and every store is coalesced. mp - 1 shifts form a full cycle, so the layout is the identity again at the end of
 // every sweep. Dg[t] and Od[t] hold A[t][t] and A[t][mp-1-t] of the current layout (written by the previous round)
-// so that rotation parameters are read from compact arrays.
+// so that rotation parameters are read from compact arrays. mp is m padded to a multiple of 32 with zero rows and
+// columns, which never rotate (their pair entries are exactly zero) and never mix with the real ones.
+//
+// Work of one round is cut into tiles of 256 threads: A tiles of 16 row pairs x 16 column pairs (one 2 x 2 block
+// per thread) and V tiles of 64 rows x 16 column pairs. A tile needs 32 rotations and a V tile 16; one warp
+// computes them into shared memory while the other threads load their blocks, so each rotation is formed once per
+// tile instead of once per block.
+constexpr int JR = 16;   // row pairs per A tile
+constexpr int JC = 16;   // column pairs per A tile and per V tile
+constexpr int JV = 64;   // rows per V tile
+
 __device__ __forceinline__ int slot_shift(int t, int mp) { return t == 0 ? 0 : (t == mp - 1 ? 1 : t + 1); }
 
 // Rotation (c, s) that annihilates apq approximately: t = tan(phi) from a single-precision solve of
-// t^2 + 2 theta t - 1 = 0 (theta = (aqq - app) / (2 apq)), then c = 1/sqrt(1 + t^2) refined by two FP64 Newton
+// t^2 + 2 theta t - 1 = 0, theta = (aqq - app) / (2 apq), then c = 1/sqrt(1 + t^2) refined by two FP64 Newton
 // steps and s = t c, so that c^2 + s^2 = 1 to FP64 rounding and the rotation is an exact orthogonal similarity.
-// (FP64 division and square root are long instruction sequences on GB300's 2-lane-per-clock FP64 pipe; the
-// residual a'_pq ~ 1e-7 |apq| left by the single-precision angle is removed by later sweeps.)
-__device__ __forceinline__ bool rot_from(double app, double aqq, double apq, double thr, double& c, double& s) {
+// theta is divided in single precision from operands scaled by inv = 1/||A||_F: |aqq - app| inv <= 2 and
+// |2 apq| inv > 2e-14 whenever a rotation is made, well inside the single-precision range. (FP64 division and
+// square root are long instruction sequences on GB300's 2-lane-per-clock FP64 pipe; the residual
+// a'_pq ~ 1e-7 |apq| left by the single-precision angle is removed by later sweeps.)
+__device__ __forceinline__ void rot_from(double app, double aqq, double apq, double thr, double inv, double& c,
+                                         double& s) {
   c = 1.0; s = 0.0;
-  if (!(fabs(apq) > thr)) return false;
-  const float th = (float)((aqq - app) / (2.0 * apq));   // FP64 quotient: no single-precision underflow
+  if (!(fabs(apq) > thr)) return;
+  const float num = (float)((aqq - app) * inv);
+  const float den = (float)((apq + apq) * inv);
+  const float th = num / den;
   const float at = fabsf(th);
   float tf = at > 1e18f ? 0.5f / at : 1.0f / (at + sqrtf(fmaf(at, at, 1.0f)));
   if (th < 0.0f) tf = -tf;
@@ -272,7 +280,6 @@ __device__ __forceinline__ bool rot_from(double app, double aqq, double apq, dou
   r = r * fma(-0.5 * q, r * r, 1.5);                 // ~1 ulp
   c = r;
   s = t * r;
-  return true;
 }
 
 __global__ void jacobi_init_kernel(const double* __restrict__ M, int m, int mp, double* A0, double* V0, double* Dg,
@@ -305,84 +312,127 @@ struct JacBuf {
   double *A[2], *V[2], *Dg[2], *Od[2];
 };
 
+// Sweeps until the matrix left by a sweep has no off-diagonal entry above the threshold (then the next sweep
+// would rotate nothing, so it is not run). The test is taken in the last round of each sweep, whose output is
+// the whole matrix in identity layout.
 __global__ void __launch_bounds__(256)
 jacobi_kernel(JacBuf b, int m, int mp, const double* normA, int* counts, int* flag, unsigned* bar, int* info) {
-  const double thr = kJacobiTol * normA[0];
+  const double nrm = normA[0];
+  const double thr = kJacobiTol * nrm;
+  const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
   const int P = mp / 2;
-  const int64_t nA = (int64_t)P * P;
-  const int64_t total = nA + (int64_t)mp * P;
+  const int TA = P / JR;
+  const int nTA = TA * TA;
+  const int nVR = (mp + JV - 1) / JV;
+  const int nT = nTA + nVR * (P / JC);
   const unsigned nb = gridDim.x;
-  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t gstride = (int64_t)nb * blockDim.x;
+  const int t = threadIdx.x;
+  __shared__ double rc[JR + JC], rs[JR + JC];
   int cur = 0;
   int sweep = 0;
+  bool converged = false;
   unsigned gen = 0;
-  for (; sweep < kJacobiMaxSweeps; ++sweep) {
+  while (sweep < kJacobiMaxSweeps && !converged) {
     for (int r = 0; r < mp - 1; ++r) {
-      const double* __restrict__ A = b.A[cur];
-      double* __restrict__ An = b.A[cur ^ 1];
-      const double* __restrict__ V = b.V[cur];
-      double* __restrict__ Vn = b.V[cur ^ 1];
-      const double* __restrict__ Dg = b.Dg[cur];
-      const double* __restrict__ Od = b.Od[cur];
-      double* __restrict__ Dn = b.Dg[cur ^ 1];
-      double* __restrict__ On = b.Od[cur ^ 1];
-      for (int64_t task = gtid; task < total; task += gstride) {
-        if (task < nA) {
-          const int ri = (int)(task % P), ci = (int)(task / P);   // row pair ri, column pair ci
+      const bool last = (r == mp - 2);
+      const double* __restrict__ A = cur ? b.A[1] : b.A[0];
+      double* __restrict__ An = cur ? b.A[0] : b.A[1];
+      const double* __restrict__ V = cur ? b.V[1] : b.V[0];
+      double* __restrict__ Vn = cur ? b.V[0] : b.V[1];
+      const double* __restrict__ Dg = cur ? b.Dg[1] : b.Dg[0];
+      const double* __restrict__ Od = cur ? b.Od[1] : b.Od[0];
+      double* __restrict__ Dn = cur ? b.Dg[0] : b.Dg[1];
+      double* __restrict__ On = cur ? b.Od[0] : b.Od[1];
+      int big = 0;
+      for (int tile = blockIdx.x; tile < nT; tile += nb) {
+        if (tile < nTA) {
+          const int R0 = (tile % TA) * JR, C0 = (tile / TA) * JC;
+          const int ri = R0 + (t % JR), ci = C0 + (t / JR);   // row pair ri, column pair ci
           const int rb = mp - 1 - ri, cb = mp - 1 - ci;
-          double cr, sr, cc, sc;
-          const bool drot = rot_from(__ldcg(Dg + ri), __ldcg(Dg + rb), __ldcg(Od + ri), thr, cr, sr);
-          rot_from(__ldcg(Dg + ci), __ldcg(Dg + cb), __ldcg(Od + ci), thr, cc, sc);
           double x00, x01, x10, x11;        // rows (ri, rb) x cols (ci, cb)
           if (ri == ci) {
             x00 = __ldcg(Dg + ri); x11 = __ldcg(Dg + rb); x01 = __ldcg(Od + ri); x10 = x01;
-            if (drot) atomicAdd(counts + sweep, 1);
           } else {
             x00 = __ldcg(A + ri + (int64_t)ci * mp); x10 = __ldcg(A + rb + (int64_t)ci * mp);
             x01 = __ldcg(A + ri + (int64_t)cb * mp); x11 = __ldcg(A + rb + (int64_t)cb * mp);
           }
+          if (t < JR + JC) {
+            const int p = t < JR ? R0 + t : C0 + (t - JR);
+            double c, s;
+            rot_from(__ldcg(Dg + p), __ldcg(Dg + mp - 1 - p), __ldcg(Od + p), thr, inv, c, s);
+            rc[t] = c;
+            rs[t] = s;
+          }
+          __syncthreads();
+          const double cr = rc[t % JR], sr = rs[t % JR], cc = rc[JR + t / JR], sc = rs[JR + t / JR];
           const double y00 = cr * x00 - sr * x10, y01 = cr * x01 - sr * x11;
           const double y10 = sr * x00 + cr * x10, y11 = sr * x01 + cr * x11;
           double z00 = cc * y00 - sc * y01, z01 = sc * y00 + cc * y01;
           double z10 = cc * y10 - sc * y11, z11 = sc * y10 + cc * y11;
           if (ri == ci) z10 = z01;                   // keep the diagonal block exactly symmetric
-          const int R0 = slot_shift(ri, mp), R1 = slot_shift(rb, mp);
-          const int C0 = slot_shift(ci, mp), C1 = slot_shift(cb, mp);
-          An[R0 + (int64_t)C0 * mp] = z00;
-          An[R1 + (int64_t)C0 * mp] = z10;
-          An[R0 + (int64_t)C1 * mp] = z01;
-          An[R1 + (int64_t)C1 * mp] = z11;
+          const int R0s = slot_shift(ri, mp), R1s = slot_shift(rb, mp);
+          const int C0s = slot_shift(ci, mp), C1s = slot_shift(cb, mp);
+          An[R0s + (int64_t)C0s * mp] = z00;
+          An[R1s + (int64_t)C0s * mp] = z10;
+          An[R0s + (int64_t)C1s * mp] = z01;
+          An[R1s + (int64_t)C1s * mp] = z11;
           // next round's diagonal and pair entries
-          if (R0 == C0) Dn[R0] = z00;
-          if (R1 == C1) Dn[R1] = z11;
-          if (R0 == C1) Dn[R0] = z01;
-          if (R1 == C0) Dn[R1] = z10;
-          if (R0 + C0 == mp - 1 && R0 < C0) On[R0] = z00;
-          if (R1 + C0 == mp - 1 && R1 < C0) On[R1] = z10;
-          if (R0 + C1 == mp - 1 && R0 < C1) On[R0] = z01;
-          if (R1 + C1 == mp - 1 && R1 < C1) On[R1] = z11;
+          if (R0s == C0s) Dn[R0s] = z00;
+          if (R1s == C1s) Dn[R1s] = z11;
+          if (R0s == C1s) Dn[R0s] = z01;
+          if (R1s == C0s) Dn[R1s] = z10;
+          if (R0s + C0s == mp - 1 && R0s < C0s) On[R0s] = z00;
+          if (R1s + C0s == mp - 1 && R1s < C0s) On[R1s] = z10;
+          if (R0s + C1s == mp - 1 && R0s < C1s) On[R0s] = z01;
+          if (R1s + C1s == mp - 1 && R1s < C1s) On[R1s] = z11;
+          if (last) {
+            big |= (R0s != C0s && fabs(z00) > thr) | (R1s != C0s && fabs(z10) > thr) |
+                   (R0s != C1s && fabs(z01) > thr) | (R1s != C1s && fabs(z11) > thr);
+          }
+          __syncthreads();                           // rc/rs are reused by the next tile
         } else {
-          const int64_t vt = task - nA;
-          const int row = (int)(vt % mp);
-          const int ci = (int)(vt / mp);
-          const int cb = mp - 1 - ci;
-          double cc, sc;
-          rot_from(__ldcg(Dg + ci), __ldcg(Dg + cb), __ldcg(Od + ci), thr, cc, sc);
-          const double vu = __ldcg(V + row + (int64_t)ci * mp), vv = __ldcg(V + row + (int64_t)cb * mp);
-          Vn[row + (int64_t)slot_shift(ci, mp) * mp] = cc * vu - sc * vv;
-          Vn[row + (int64_t)slot_shift(cb, mp) * mp] = sc * vu + cc * vv;
+          const int v = tile - nTA;
+          const int R0 = (v % nVR) * JV, C0 = (v / nVR) * JC;
+          const int ci = C0 + t / 16, cb = mp - 1 - ci;
+          double vu[JV / 16], vv[JV / 16];
+#pragma unroll
+          for (int j = 0; j < JV / 16; ++j) {
+            const int row = R0 + (t % 16) + 16 * j;
+            vu[j] = row < mp ? __ldcg(V + row + (int64_t)ci * mp) : 0.0;
+            vv[j] = row < mp ? __ldcg(V + row + (int64_t)cb * mp) : 0.0;
+          }
+          if (t < JC) {
+            const int p = C0 + t;
+            double c, s;
+            rot_from(__ldcg(Dg + p), __ldcg(Dg + mp - 1 - p), __ldcg(Od + p), thr, inv, c, s);
+            rc[t] = c;
+            rs[t] = s;
+          }
+          __syncthreads();
+          const double cc = rc[t / 16], sc = rs[t / 16];
+          const int c0 = slot_shift(ci, mp), c1 = slot_shift(cb, mp);
+#pragma unroll
+          for (int j = 0; j < JV / 16; ++j) {
+            const int row = R0 + (t % 16) + 16 * j;
+            if (row < mp) {
+              Vn[row + (int64_t)c0 * mp] = cc * vu[j] - sc * vv[j];
+              Vn[row + (int64_t)c1 * mp] = sc * vu[j] + cc * vv[j];
+            }
+          }
+          __syncthreads();
         }
       }
+      if (last && __syncthreads_or(big) && t == 0) atomicOr(counts + sweep, 1);
       if (!grid_sync(bar, nb, flag, gen)) return;
       cur ^= 1;
     }
-    if (ld_relaxed_gpu(counts + sweep) == 0) break;
+    converged = ld_relaxed_gpu(counts + sweep) == 0;
+    ++sweep;
   }
-  if (gtid == 0) {
-    info[0] = sweep;
+  if (blockIdx.x == 0 && t == 0) {
+    info[0] = sweep;                                 // sweeps run
     info[1] = cur;
-    if (sweep >= kJacobiMaxSweeps) atomicOr(flag, kFlagJacobiNoConv);
+    if (!converged) atomicOr(flag, kFlagJacobiNoConv);
   }
 }
 
@@ -434,7 +484,7 @@ CoopLimit& coop_limits() {
 }
 
 inline int pad_tile(int m) { return (int)ceil_div(m, TB) * TB; }
-inline int pad_even(int m) { return (m + 1) & ~1; }
+inline int pad_jac(int m) { return (int)ceil_div(m < 2 ? 2 : m, 32) * 32; }
 
 }  // namespace
 
@@ -452,30 +502,29 @@ cudaError_t chol_inv(const double* G, int m, double shift, double* Rinv, double*
   const int T = mp / TB;
   double* Lw = ws;
   double* Linv = Lw + (size_t)mp * mp;
-  double* Dinv = Linv + (size_t)mp * mp;
-  double* diag0 = Dinv + (size_t)mp * TB;
+  double* Lp = Linv + (size_t)mp * mp;
+  double* diag0 = Lp + (size_t)mp * TB;
   cudaError_t e = cudaMemsetAsync(bar, 0, barrier_words() * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  int tasks = T * (T - 1) / 2;
-  if (tasks < T) tasks = T;
-  if (tasks < 1) tasks = 1;
+  int tasks = 2 * (T - 1) * (T + 2);                  // update tasks of the first step (the most)
+  if (tasks < 4 * T) tasks = 4 * T;
   const int lim = coop_limits().chol;
   const int grid = tasks < lim ? tasks : lim;
   void* args[] = {(void*)&G, (void*)&m, (void*)&mp, (void*)&shift, (void*)&Rinv, (void*)&Lw,
-                  (void*)&Linv, (void*)&Dinv, (void*)&diag0, (void*)&flag, (void*)&bar};
+                  (void*)&Linv, (void*)&Lp, (void*)&diag0, (void*)&flag, (void*)&bar};
   count_launch();
   return cudaLaunchCooperativeKernel((const void*)chol_inv_kernel, dim3(grid), dim3(256), args, 0, s);
 }
 
 size_t jacobi_ws_elems(int m) {
-  const size_t mp = (size_t)pad_even(m < 2 ? 2 : m);
+  const size_t mp = (size_t)pad_jac(m);
   return 4 * mp * mp + 4 * mp + 8 + (size_t)kJacobiMaxSweeps + mp + 8;
 }
 
 cudaError_t jacobi_eigh(const double* M, int m, double* lambda, double* C, double* ws, int* flag, unsigned* bar,
                         int* sweeps_out_dev, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
-  const int mp = pad_even(m < 2 ? 2 : m);
+  const int mp = pad_jac(m);
   JacBuf jb;
   double* p = ws;
   for (int i = 0; i < 2; ++i) { jb.A[i] = p; p += (size_t)mp * mp; }
@@ -499,8 +548,7 @@ cudaError_t jacobi_eigh(const double* M, int m, double* lambda, double* C, doubl
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int P = mp / 2;
-  const int64_t total = (int64_t)P * P + (int64_t)mp * P;
-  const int64_t want = ceil_div(total, 256);
+  const int64_t want = (int64_t)(P / JR) * (P / JR) + ceil_div(mp, JV) * (P / JC);
   const int lim = coop_limits().jac;
   const int grid = (int)(want < lim ? (want < 1 ? 1 : want) : lim);
   const double* nrm_c = nrm;
