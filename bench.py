@@ -175,6 +175,25 @@ def run_reference(args, w):
     return 0
 
 
+# form name -> (precision, how the FP64 n x k GEMMs run, step-18 orthonormalisation)
+FORMS = {
+    "fp64": ("fp64", "fma", "cholqr2"),
+    "mixed": ("mixed_tf32", "fma", "cholqr2"),
+    "fp64_ozaki": ("fp64", "ozaki", "cholqr2"),
+    "mixed_ozaki": ("mixed_tf32", "ozaki", "cholqr2"),
+    "fp64_ozaki_polar": ("fp64", "ozaki", "polar"),
+    "mixed_ozaki_polar": ("mixed_tf32", "ozaki", "polar"),
+}
+FORM_TEXT = {
+    "fp64": "FP64 throughout (FP64 FMA pipe GEMMs), CholeskyQR2",
+    "mixed": "TF32 tcgen05 projection GEMMs and first CholeskyQR Gram; everything else FP64",
+    "fp64_ozaki": "FP64 with the n x k GEMMs emulated on BF16 tcgen05 (8 digit slices, Ozaki)",
+    "mixed_ozaki": "mixed (TF32 projections) with the other FP64 n x k GEMMs emulated on BF16 tcgen05 (Ozaki)",
+    "fp64_ozaki_polar": "fp64_ozaki with the polar-series orthonormalisation of Section 5.4",
+    "mixed_ozaki_polar": "mixed_ozaki with the polar-series orthonormalisation of Section 5.4",
+}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -187,8 +206,8 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=3, help="oracle iterations in the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--forms", default="fp64,mixed,fp64_ozaki,mixed_ozaki",
-                    help="forms to time; the first is the headline value (fp64, mixed, fp64_ozaki, mixed_ozaki)")
+    ap.add_argument("--forms", default="fp64,mixed,fp64_ozaki,mixed_ozaki,mixed_ozaki_polar",
+                    help="forms to time; the first is the headline value (" + ", ".join(FORMS) + ")")
     args = ap.parse_args()
     w = wl.CONFIGS[int(args.workload)]
     if args.impl == "reference":
@@ -215,9 +234,9 @@ def main():
     X0_d = torch.from_numpy(np.ascontiguousarray(X0.T)).to(dev)         # (k, n) rows = columns of X0
     _, gold = oracle_full_iters()
 
-    def run_form(precision, clk_sampler, fp64_gemm="fma"):
+    def run_form(precision, clk_sampler, fp64_gemm="fma", orth="cholqr2"):
         solver = pk.Solver(V_d, w.N, w.k, w.sbsize, rr_period=w.rr_period, maxiter=args.maxiter, device=dev,
-                           stream=stream, precision=precision, fp64_gemm=fp64_gemm)
+                           stream=stream, precision=precision, fp64_gemm=fp64_gemm, orth=orth)
         X_out = torch.empty((w.k, w.n), dtype=torch.float64, device=dev)
         for _ in range(args.warmup):
             solver.solve(X0_d, w.tol, out=X_out)
@@ -250,26 +269,24 @@ def main():
         solver.close()
         # one more solve with per-phase timers (the paper's profile categories), outside the timed region
         ps = pk.Solver(V_d, w.N, w.k, w.sbsize, rr_period=w.rr_period, maxiter=args.maxiter, device=dev,
-                       stream=stream, timing=True, precision=precision, fp64_gemm=fp64_gemm)
+                       stream=stream, timing=True, precision=precision, fp64_gemm=fp64_gemm, orth=orth)
         _, _, _, pst = ps.solve(X0_d, w.tol)
         ps.close()
         return {"ms_per_step": ms / args.steps, "iters": iters // args.steps, "iters_per_s": iters / (ms / 1e3),
                 "wall_s_per_step": wall / args.steps, "launches": launches, "parity": parity,
                 "phase_ms": {k_: round(v_, 2) for k_, v_ in pst["t_phase_ms"].items()},
-                "jacobi_sweeps_max": pst["jacobi_sweeps_max"]}
+                "jacobi_sweeps_max": pst["jacobi_sweeps_max"],
+                "counts": {k_: stats[-1][k_] for k_ in ("n_rr", "n_drop_p", "n_cholqr_fallback", "n_polar",
+                                                         "n_orth_skip")}}
 
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     clk = ClockSampler(local)
     first = forms[0]
-    spec = {"fp64": ("fp64", "fma"), "mixed": ("mixed_tf32", "fma"), "fp64_ozaki": ("fp64", "ozaki"),
-            "mixed_ozaki": ("mixed_tf32", "ozaki")}
     results = {}
     for f in forms:
-        prec, gm = spec[f]
-        results[f] = run_form(prec, clk if f == first else ClockSampler(local), fp64_gemm=gm)
+        prec, gm, orth = FORMS[f]
+        results[f] = run_form(prec, clk if f == first else ClockSampler(local), fp64_gemm=gm, orth=orth)
     fp64 = results[first]
-    mixed = results.get("mixed")
-    emu = {k.split("_")[0]: v for k, v in results.items() if k.endswith("_ozaki")}
     ms_per_step = fp64["ms_per_step"]
     iters = fp64["iters"] * args.steps
     launches = fp64["launches"]
@@ -279,7 +296,7 @@ def main():
     roof = roofline(pk, probe, w, dev, stream)
     probe.close()
     roof_mixed = None
-    if mixed is not None or "mixed_ozaki" in results:
+    if any(FORMS[f][0] == "mixed_tf32" for f in results):
         probe = pk.Solver(V_d, w.N, w.k, w.sbsize, rr_period=w.rr_period, maxiter=1, device=dev, stream=stream,
                           precision="mixed_tf32")
         roof_mixed = roofline_tc(pk, probe, w, dev, stream)
@@ -300,19 +317,15 @@ def main():
         "iters": fp64["iters"], "iters_per_s": fp64["iters_per_s"], "wall_s_per_step": fp64["wall_s_per_step"],
         "parity": parity, "roofline": roof, "phase_ms": phases, "jacobi_sweeps_max": fp64["jacobi_sweeps_max"],
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
-        "mixed": None if mixed is None else {
-            "form": "TF32 tcgen05 projection GEMMs and first CholeskyQR Gram; everything else FP64",
-            "value": mixed["ms_per_step"] / 1e3, "unit": "s", "iters": mixed["iters"],
-            "iters_per_s": mixed["iters_per_s"], "speedup_vs_fp64": fp64["ms_per_step"] / mixed["ms_per_step"],
-            "parity": mixed["parity"], "phase_ms": mixed["phase_ms"], "gpu_launches": mixed["launches"],
-            "roofline": roof_mixed},
-        "fp64_gemm_emulated": {
-            name: {"form": ("FP64" if name == "fp64" else "mixed (TF32 projections)") +
-                           " with every other FP64 n x k GEMM emulated on BF16 tcgen05 (8 digit slices, Ozaki)",
-                   "value": f["ms_per_step"] / 1e3, "unit": "s", "iters": f["iters"], "iters_per_s": f["iters_per_s"],
-                   "speedup_vs_fp64": fp64["ms_per_step"] / f["ms_per_step"], "parity": f["parity"],
-                   "phase_ms": f["phase_ms"], "gpu_launches": f["launches"]}
-            for name, f in emu.items()},
+        "counts": fp64["counts"],
+        "forms": {
+            name: {"form": FORM_TEXT[name], "value": f["ms_per_step"] / 1e3, "unit": "s", "iters": f["iters"],
+                   "iters_per_s": f["iters_per_s"],
+                   "speedup_vs_fp64": (results["fp64"]["ms_per_step"] / f["ms_per_step"]) if "fp64" in results else None,
+                   "parity": f["parity"], "phase_ms": f["phase_ms"], "gpu_launches": f["launches"],
+                   "counts": f["counts"]}
+            for name, f in results.items()},
+        "roofline_tf32_gram": roof_mixed,
     }
     print(json.dumps(line), flush=True)
     if dist:

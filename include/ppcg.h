@@ -72,7 +72,12 @@ typedef struct {
                            kind 1 = Rayleigh-Ritz step (value = max_i r_i, trace = sum of the k Ritz values) */
   int32_t fp64_gemm;    /* [0] how the FP64 n x k GEMMs run: 0 = FP64 FMA pipe, 1 = FP64-accurate emulation on
                            the BF16 tensor cores (error-free splitting into 8 digit slices, Ozaki scheme) */
-  int32_t reserved[5];
+  int32_t orth;         /* [0] step 18 (Section 5.4): 0 = CholeskyQR2; 1 = polar X <- X (X^T X)^{-1/2} by the
+                           series of (I + Y)^{-1/2}, Y = X^T X - I, with the fewest terms (at most 8) whose first
+                           omitted term nu^{t+1} |c_{t+1}| is below the FP64 unit roundoff, nu = ||Y||_F; when no
+                           such t exists CholeskyQR2 runs instead */
+  double orth_skip_tol; /* [0] skip step 18 when ||X^T X - I||_F <= orth_skip_tol (Section 5.4); 0 never skips */
+  int32_t reserved[2];
 } ppcg_options;
 
 /* Phases of the per-phase times, after the paper's profile categories (Tables Li318prof, Siprof) */
@@ -93,6 +98,8 @@ typedef struct {
   int64_t kernel_launches;    /* device kernels this solve launched */
   double t_phase_ms[8];       /* per-phase device time (ms) when options.timing = 1 */
   double max_res;             /* max_i ||A x_i - lambda_i x_i|| over the k returned pairs */
+  int32_t n_orth_skip;        /* plain steps whose orthonormalisation was skipped (options.orth_skip_tol) */
+  int32_t n_polar;            /* plain steps orthonormalised by the polar series (options.orth = 1) */
 } ppcg_stats;
 
 typedef struct ppcg_ctx* ppcg_handle;

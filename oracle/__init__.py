@@ -7,5 +7,5 @@ with the CUDA library: it reads only the seeded inputs from the standalone `work
 from .ppcg import (  # noqa: F401
     apply_H, diag_H, assemble_H, precondition, project, cholqr, cholqr2, shifted_cholqr3,
     block_coefficients, block_update, rayleigh_ritz, residual, ppcg, PPCGResult, normalize_phase,
-    subblocks, orth, energy_gradient,
+    subblocks, orth, energy_gradient, polar_coefficients, polar_terms, orth_polar, orthonormalize, POLAR_MAX_TERMS,
 )

@@ -32,6 +32,12 @@ Readings of the paper taken where it is silent (each is restated where it is use
       Rayleigh-Ritz step through S = [X, X_lock] (soft locking, Section 5.6).
   R9  output: Ritz values ascending; each Ritz vector has unit norm and its entry of largest modulus
       (lowest index on ties) real and positive.
+  R10 orthonormalisation variants of Section 5.4 (optional; the default is CholeskyQR2 every plain step):
+      "polar" replaces step 18 by X <- X (X* X)^{-1/2}, the (X* X)^{-1/2} = (I + Y)^{-1/2} series in
+      Y = X* X - I truncated after t terms, t the fewest (at most POLAR_MAX_TERMS) whose first omitted term
+      |c_{t+1}| nu^{t+1} is below the FP64 unit roundoff, nu = ||Y||_F; when no such t exists (nu too large
+      for the series) CholeskyQR2 is used. "skip" (orth_skip_tol > 0) leaves X as it is when nu <= orth_skip_tol,
+      the loss-of-orthogonality heuristic of the same section.
 """
 from __future__ import annotations
 
@@ -44,6 +50,7 @@ import scipy.linalg as sla
 PIVOT_TOL = 1e-7       # R6: smallest Cholesky diagonal of the unit-diagonal S_j* S_j (squared pivot 1e-14)
 ALPHA_TOL = 1e-12      # R6: smallest singular value of C_X (|alpha_j| for q = 1), Theorem 1
 CHOL_PIVOT_TOL = 1e-7  # R5: smallest relative Cholesky pivot R_ii / sqrt(G_ii) accepted by CholQR
+POLAR_MAX_TERMS = 8    # R10: most series terms the polar variant may use
 
 
 # --------------------------------------------------------------------------------------------------------
@@ -182,6 +189,57 @@ def orth(X, stats=None):
         return shifted_cholqr3(X)[0]
 
 
+def polar_coefficients(t):
+    """c_0..c_t of the binomial series (1 + y)^{-1/2} = sum_j c_j y^j, c_j = binom(-1/2, j) (Section 5.4)."""
+    c = [1.0]
+    for j in range(1, t + 1):
+        c.append(c[-1] * (-(2 * j - 1) / (2 * j)))
+    return np.array(c)
+
+
+def polar_terms(nu, tmax=POLAR_MAX_TERMS):
+    """Reading R10: the fewest terms t >= 1 whose first omitted series term |c_{t+1}| nu^{t+1} is below the FP64
+    unit roundoff, or None when even tmax terms leave a larger one."""
+    c = polar_coefficients(tmax + 1)
+    u = np.finfo(np.float64).eps / 2
+    for t in range(1, tmax + 1):
+        if abs(c[t + 1]) * nu ** (t + 1) <= u:
+            return t
+    return None
+
+
+def orth_polar(X, t):
+    """X <- X (I + Y)^{-1/2} with the series truncated after t terms, Y = X* X - I (Section 5.4)."""
+    m = X.shape[1]
+    Y = X.conj().T @ X - np.eye(m)
+    c = polar_coefficients(t)
+    C = np.zeros((m, m), dtype=X.dtype)
+    Yj = np.eye(m, dtype=X.dtype)
+    for j in range(t + 1):                       # sum_j c_j Y^j with explicit powers
+        C = C + c[j] * Yj
+        Yj = Yj @ Y
+    return np.asfortranarray(X @ C)
+
+
+def orthonormalize(X, mode="cholqr2", skip_tol=0.0, stats=None):
+    """Step 18 with the variants of reading R10. mode "cholqr2" with skip_tol = 0 is plain orth(X)."""
+    if mode == "cholqr2" and not skip_tol > 0.0:
+        return orth(X, stats)
+    m = X.shape[1]
+    nu = np.linalg.norm(X.conj().T @ X - np.eye(m))
+    if nu <= skip_tol:
+        if stats is not None:
+            stats["n_orth_skip"] = stats.get("n_orth_skip", 0) + 1
+        return X
+    if mode == "polar":
+        t = polar_terms(nu)
+        if t is not None:
+            if stats is not None:
+                stats["n_polar"] = stats.get("n_polar", 0) + 1
+            return orth_polar(X, t)
+    return orth(X, stats)
+
+
 def subblocks(k_act, q):
     """Sub-block column ranges: s = ceil(k_act / q) blocks of q columns, the last one the remainder
     (Section 5.1; Alg. 3 step 5 footnote)."""
@@ -318,11 +376,12 @@ class PPCGResult:
 
 
 def ppcg(V, N, h, k, sbsize, rr_period, X0, tol=1e-8, maxiter=500, nbuf=0, lock=True, theta=None,
-         sigma_floor=None, project_W=True, project_P=True, verbose=False):
+         sigma_floor=None, project_W=True, project_P=True, verbose=False, orth_mode="cholqr2", orth_skip_tol=0.0):
     """PPCG (Algorithm 3) for the k algebraically smallest eigenpairs of A = -Laplacian_h + diag(V).
 
     X0 is n x (k + nbuf). Returns a PPCGResult; `project_W` / `project_P` switch off the projections of
-    steps 9 / 10 for the ablation of Section 5.4 (figure "proj").
+    steps 9 / 10 for the ablation of Section 5.4 (figure "proj"); `orth_mode` ("cholqr2" or "polar") and
+    `orth_skip_tol` select the step-18 variants of reading R10.
     """
     V = np.asarray(V, dtype=np.float64)
     n = N ** 3
@@ -330,7 +389,8 @@ def ppcg(V, N, h, k, sbsize, rr_period, X0, tol=1e-8, maxiter=500, nbuf=0, lock=
     assert X0.shape == (n, kt)
     q = sbsize
     delta = 0.1 / (h * h) if sigma_floor is None else sigma_floor
-    stats = {"n_drop_p": 0, "n_stall": 0, "n_cholqr_fallback": 0, "n_locked": 0, "n_early_rr": 0}
+    stats = {"n_drop_p": 0, "n_stall": 0, "n_cholqr_fallback": 0, "n_locked": 0, "n_early_rr": 0,
+             "n_orth_skip": 0, "n_polar": 0}
     phase = {"AX": 0.0, "GEMM": 0.0, "BlockRR": 0.0, "CholQR": 0.0, "RR": 0.0, "Precond": 0.0, "Lock": 0.0}
     history = []
 
@@ -416,7 +476,7 @@ def ppcg(V, N, h, k, sbsize, rr_period, X0, tol=1e-8, maxiter=500, nbuf=0, lock=
         if it % rr_period != 0:
             # Steps 18-20: X <- orth(X); W <- A X - X (X* A X)
             t = time.perf_counter()
-            X = orth(X, stats)
+            X = orthonormalize(X, orth_mode, orth_skip_tol, stats)
             phase["CholQR"] += time.perf_counter() - t
             HX = Hop(X)
             t = time.perf_counter()

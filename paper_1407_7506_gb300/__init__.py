@@ -39,7 +39,8 @@ class ppcg_options(ctypes.Structure):
     _fields_ = [("maxiter", ctypes.c_int32), ("nbuf", ctypes.c_int32), ("no_lock", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("sigma_floor", ctypes.c_double), ("timing", ctypes.c_int32),
                 ("history_cap", ctypes.c_int32), ("history", ctypes.POINTER(ctypes.c_double)),
-                ("fp64_gemm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("fp64_gemm", ctypes.c_int32), ("orth", ctypes.c_int32), ("orth_skip_tol", ctypes.c_double),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class ppcg_stats(ctypes.Structure):
@@ -47,7 +48,7 @@ class ppcg_stats(ctypes.Structure):
                 ("n_drop_p", ctypes.c_int32), ("n_stall", ctypes.c_int32), ("n_cholqr_fallback", ctypes.c_int32),
                 ("n_early_rr", ctypes.c_int32), ("converged", ctypes.c_int32), ("history_len", ctypes.c_int32),
                 ("jacobi_sweeps_max", ctypes.c_int32), ("kernel_launches", ctypes.c_int64), ("t_phase_ms", ctypes.c_double * 8),
-                ("max_res", ctypes.c_double)]
+                ("max_res", ctypes.c_double), ("n_orth_skip", ctypes.c_int32), ("n_polar", ctypes.c_int32)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "t_phase_ms"}

@@ -149,6 +149,8 @@ ppcg_status check_args(const ppcg_operator* op, int64_t n, int32_t k, int32_t sb
   if (opt && (opt->maxiter < 0 || opt->sigma_floor < 0.0)) return PPCG_ERR_ARG;
   if (opt && opt->precision != PPCG_FP64 && opt->precision != PPCG_MIXED_TF32) return PPCG_ERR_UNSUPPORTED;
   if (opt && (opt->fp64_gemm < 0 || opt->fp64_gemm > 1)) return PPCG_ERR_ARG;
+  if (opt && (opt->orth < 0 || opt->orth > 1)) return PPCG_ERR_ARG;
+  if (opt && !(opt->orth_skip_tol >= 0.0 && std::isfinite(opt->orth_skip_tol))) return PPCG_ERR_ARG;
   return PPCG_OK;
 }
 
@@ -332,6 +334,58 @@ int last_sweeps(ppcg_ctx* c) {
   return info[0];
 }
 
+// Terms of the polar series: the fewest t >= 1 with |c_{t+1}| nu^{t+1} <= u (FP64 unit roundoff), 0 if none
+// within kPolarMaxTerms. c_j = binom(-1/2, j) by c_j = c_{j-1} (-(2j - 1) / (2j)).
+int polar_terms(double nu, double* coef) {
+  coef[0] = 1.0;
+  for (int j = 1; j <= kPolarMaxTerms + 1; ++j) coef[j] = coef[j - 1] * (-(2.0 * j - 1.0) / (2.0 * j));
+  const double u = 1.1102230246251565e-16;
+  for (int t = 1; t <= kPolarMaxTerms; ++t)
+    if (std::fabs(coef[t + 1]) * std::pow(nu, t + 1) <= u) return t;
+  return 0;
+}
+
+// Step 18 with the variants of Section 5.4: CholeskyQR2, the polar series X (I + Y)^{-1/2} (Y = X^T X - I, FP64
+// Gram in every form), or no orthonormalisation when ||Y||_F <= orth_skip_tol.
+ppcg_status orthonormalize(ppcg_ctx* c, double* X, int64_t ldx, double* Xs, int64_t ldxs, int m, ppcg_stats* S) {
+  const bool variant = c->opt.orth != 0 || c->opt.orth_skip_tol > 0.0;
+  if (variant && m > 0) {
+    PS(gram(c, X, ldx, X, ldx, m, m, c->G, m));
+    CK(eye_residual(c->G, m, c->C, c->stream));                  // Y = G - I in G, ||Y||_F^2 in C[0]
+    double nu2 = 0.0;
+    CK(cudaMemcpyAsync(&nu2, c->C, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (!std::isfinite(nu2)) return PPCG_ERR_NUMERIC;
+    const double nu = std::sqrt(nu2);
+    if (nu <= c->opt.orth_skip_tol) {
+      S->n_orth_skip++;
+      return PPCG_OK;
+    }
+    double coef[kPolarMaxTerms + 2];
+    const int t = c->opt.orth == 1 ? polar_terms(nu, coef) : 0;
+    if (t > 0) {
+      // Horner: Z = c_t Y + c_{t-1} I; Z <- Y Z + c_j I for j = t-2 .. 0 (Y in G; Z alternates M / Rinv)
+      double* Z = c->M;
+      double* Zn = c->Rinv;
+      CK(scaled_plus_identity(c->G, m, coef[t], coef[t - 1], Z, c->stream));
+      for (int j = t - 2; j >= 0; --j) {
+        CK(small_gemm(false, c->G, m, Z, m, m, m, m, Zn, m, c->gpart, c->gpart_cap, c->stream));
+        CK(add_diag(Zn, m, coef[j], c->stream));
+        std::swap(Z, Zn);
+      }
+      PS(update(c, X, ldx, Z, m, m, m, Xs, ldxs, Epi::Store, false));
+      CK(cudaMemcpy2DAsync(X, ldx * sizeof(double), Xs, ldxs * sizeof(double), c->n * sizeof(double), m,
+                           cudaMemcpyDeviceToDevice, c->stream));
+      S->n_polar++;
+      return PPCG_OK;
+    }
+  }
+  int fb = 0;
+  PS(cholqr2(c, X, ldx, Xs, ldxs, m, &fb));
+  if (fb) S->n_cholqr_fallback++;
+  return PPCG_OK;
+}
+
 ResidualArgs resid_args(ppcg_ctx* c, double sigma) {
   ResidualArgs ra{};
   ra.dg = c->dg;
@@ -373,8 +427,8 @@ ppcg_status rr_step(ppcg_ctx* c, SolveState& st, bool allow_compact, ppcg_stats*
   CK(cudaMemsetAsync(rrflag, 0, sizeof(int), s));
   CK(chol_inv(c->G, kt, 0.0, c->Rinv, c->cholws, rrflag, c->bar, s));  // R^{-1}
   // K = R^{-T} (S^T A S) R^{-1}: T = (S^T A S) R^{-1} (R^{-1} upper: trimmed K loop), K = (R^{-1})^T T
-  CK(gemm_nn(c->M, kt, c->Rinv, kt, kt, kt, kt, c->G, kt, nullptr, 0, Epi::Store, true, nullptr, s));
-  CK(ppcg::gram(c->Rinv, kt, c->G, kt, kt, kt, kt, c->M, kt, false, c->gpart, c->gpart_cap, s));
+  CK(small_gemm(false, c->M, kt, c->Rinv, kt, kt, kt, kt, c->G, kt, c->gpart, c->gpart_cap, s));
+  CK(small_gemm(true, c->Rinv, kt, c->G, kt, kt, kt, kt, c->M, kt, c->gpart, c->gpart_cap, s));
   PS(dense_eigh(c, c->M, kt, c->lam, c->C));
   // sigma = smallest Ritz value of this step: the host needs it for the preconditioner
   CK(cudaMemcpyAsync(c->lam_h.data(), c->lam, sizeof(double) * kt, cudaMemcpyDeviceToHost, s));
@@ -399,7 +453,7 @@ ppcg_status rr_step(ppcg_ctx* c, SolveState& st, bool allow_compact, ppcg_stats*
     if (fl[0] & kFlagTimeout) return PPCG_ERR_TIMEOUT;
   } else {
     // coefficients R^{-1} Z (R^{-1} is upper triangular)
-    CK(gemm_nn(c->Rinv, kt, c->C, kt, kt, kt, kt, c->G, kt, nullptr, 0, Epi::Store, false, nullptr, s));
+    CK(small_gemm(false, c->Rinv, kt, c->C, kt, kt, kt, kt, c->G, kt, c->gpart, c->gpart_cap, s));
   }
   PS(update(c, c->X, c->ld, c->G, kt, kt, kt, c->Xs, c->ld, Epi::Store, false));
   swap(c->X, c->Xs);
@@ -670,9 +724,7 @@ ppcg_status ppcg_solve(ppcg_handle c, const double* X0, double tol, double* lamb
     if (!do_rr) {
       // steps 18-20
       phase_mark(c, PPCG_T_CHOLQR);
-      fb = 0;
-      PS(cholqr2(c, Xa, ld, c->Xs + (int64_t)kl * ld, ld, ka, &fb));
-      if (fb) S->n_cholqr_fallback++;
+      PS(orthonormalize(c, Xa, ld, c->Xs + (int64_t)kl * ld, ld, ka, S));
       phase_mark(c, PPCG_T_AX);
       PS(apply_H(c, Xa, ld, HXa, ld, ka));
       phase_mark(c, PPCG_T_GEMM);

@@ -6,6 +6,7 @@
 //            Used by steps 9-10 (X^T W, X^T P), 18 (X^T X), 20 (X^T AX) and 23 (S^T AS).
 //   gemm_nn  Y (+)= A G with A: n x m, G: m x p small; epilogues for steps 9-10 (Y - X G, in place),
 //            19 / 24 (X R^{-1}, S C) and 20 + 8 fused (W = T (AX - X M) with column norms of the residual).
+//   small_gemm  C = op(A) B for the k x k products (steps 23-24, polar step 18), split over K.
 //
 // On GB300 FP64 runs at 2 DFMA lanes per clock per SM (measured 1.195 TFLOP/s for the whole GPU), so these
 // GEMMs, with arithmetic intensity k/8 flop/byte, are FP64-pipe bound by a wide margin; the tiling only has to
@@ -173,6 +174,59 @@ gemm_nn_kernel(const double* __restrict__ A, int64_t lda, const double* __restri
   }
 }
 
+// part[split][i + j*m] = sum over the split's K range of op(A)[i, l] * B[l, j], op(A) = A^T (TRANS) or A.
+// The k x k products of Algorithm 3 (steps 23-24 and the polar variant of step 18) have K = k only, too short
+// for a 64 x 64 tile per CTA to fill the GPU; splitting K into 32-deep chunks gives 8x more CTAs at k = 256.
+template <bool TRANS>
+__global__ void __launch_bounds__(kThreads)
+small_gemm_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ B, int64_t ldb, int m,
+                  int p, int kdim, int tiles_p, int k_per_split, double* __restrict__ part) {
+  const int ti = blockIdx.x / tiles_p, tj = blockIdx.x % tiles_p;
+  const int i0 = ti * kT, j0 = tj * kT;
+  const int k_begin = blockIdx.y * k_per_split;
+  const int k_end = min(kdim, k_begin + k_per_split);
+  __shared__ __align__(16) double As[kBK][kT + kPad];
+  __shared__ __align__(16) double Bs[kBK][kT + kPad];
+  const int t = threadIdx.x;
+  const int tr = t % 16, tc = t / 16;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int k0 = k_begin; k0 < k_end; k0 += kBK) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (TRANS) {                                   // A^T: K index runs down A's columns (coalesced in K)
+        const int lk = t % kBK, cc = t / kBK + 16 * u;
+        const int kk = k0 + lk;
+        As[lk][cc] = (kk < k_end && i0 + cc < m) ? __ldg(A + kk + (int64_t)(i0 + cc) * lda) : 0.0;
+      } else {                                       // A: rows i are contiguous
+        const int cc = t % kT, lk = t / kT + 4 * u;
+        const int kk = k0 + lk;
+        As[lk][cc] = (kk < k_end && i0 + cc < m) ? __ldg(A + (i0 + cc) + (int64_t)kk * lda) : 0.0;
+      }
+      const int lk = t % kBK, cc = t / kBK + 16 * u;
+      const int kk = k0 + lk;
+      Bs[lk][cc] = (kk < k_end && j0 + cc < p) ? __ldg(B + kk + (int64_t)(j0 + cc) * ldb) : 0.0;
+    }
+    __syncthreads();
+    fma_tile(As, Bs, tr * 4, tc * 4, acc);
+    __syncthreads();
+  }
+  double* out = part + (int64_t)blockIdx.y * m * p;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gi = i0 + tr * 4 + i;
+    if (gi >= m) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gj = j0 + tc * 4 + j;
+      if (gj < p) out[gi + (int64_t)gj * m] = acc[i][j];
+    }
+  }
+}
+
 int grid_sm_count() {
   static int sms = 0;
   if (sms == 0) {
@@ -229,6 +283,28 @@ cudaError_t gram_reduce_partials(const double* part, int nsplit, int ma, int mb,
                                                                                 symmetric ? 1 : 0);
   count_launch();
   return cudaGetLastError();
+}
+
+cudaError_t small_gemm(bool trans_a, const double* A, int64_t lda, const double* B, int64_t ldb, int m, int p,
+                       int kdim, double* C, int ldc, double* part, size_t part_capacity, cudaStream_t s) {
+  if (m <= 0 || p <= 0) return cudaSuccess;
+  if (kdim <= 0 || (size_t)m * p > part_capacity) return cudaErrorInvalidValue;
+  int nsplit = (int)ceil_div(kdim, 32);
+  const int64_t cap = (int64_t)(part_capacity / ((size_t)m * p));
+  if (nsplit > cap) nsplit = (int)cap;
+  int kps = (int)ceil_div(kdim, nsplit);
+  kps = (int)ceil_div(kps, kBK) * kBK;
+  nsplit = (int)ceil_div(kdim, kps);
+  const int tiles_m = (int)ceil_div(m, kT), tiles_p = (int)ceil_div(p, kT);
+  dim3 grid(tiles_m * tiles_p, nsplit);
+  if (trans_a)
+    small_gemm_kernel<true><<<grid, kThreads, 0, s>>>(A, lda, B, ldb, m, p, kdim, tiles_p, kps, part);
+  else
+    small_gemm_kernel<false><<<grid, kThreads, 0, s>>>(A, lda, B, ldb, m, p, kdim, tiles_p, kps, part);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return gram_reduce_partials(part, nsplit, m, p, C, ldc, false, s);
 }
 
 cudaError_t gemm_nn(const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p, double* Y,

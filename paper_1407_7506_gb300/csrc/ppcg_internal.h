@@ -16,6 +16,7 @@ constexpr double kJacobiTol = 1e-14;    // k x k Jacobi: rotate while |a_pq| > k
                                         // left below that adds < ~1e-12 to a Ritz residual (tol is 1e-8)
 constexpr double kJacobiTolSmall = 1e-16;  // sub-block warp Jacobi
 constexpr int kJacobiMaxSweeps = 60;
+constexpr int kPolarMaxTerms = 8;        // most series terms of the polar orthonormalisation
 constexpr int kMaxSbsize = 16;          // 3q <= 48 fits the warp-level sub-block solver
 
 // Error-flag bits written by kernels into the handle's device flag word.
@@ -46,6 +47,11 @@ cudaError_t gram(const double* A, int64_t lda, const double* B, int64_t ldb, int
                  int ldc, bool symmetric, double* part, size_t part_capacity, cudaStream_t s);
 
 enum class Epi : int { Store = 0, Sub = 1, Residual = 2 };
+
+// C = op(A) B (m x p, K = kdim; op(A) = A^T when trans_a) for small square-ish operands, split over K with a
+// deterministic reduction; part holds the split partials (part_capacity doubles).
+cudaError_t small_gemm(bool trans_a, const double* A, int64_t lda, const double* B, int64_t ldb, int m, int p,
+                       int kdim, double* C, int ldc, double* part, size_t part_capacity, cudaStream_t s);
 struct ResidualArgs {
   const double* dg;     // 6/h^2 + V
   double sigma;         // preconditioner shift
@@ -101,6 +107,11 @@ cudaError_t density(const double* X, int64_t ld, int64_t n, int k, double scale,
 cudaError_t make_diag(const double* V, double inv_h2, int64_t n, double* dg, cudaStream_t s);
 // count non-finite entries of v[0..m) into *bad (device int)
 cudaError_t check_finite(const double* v, int m, int* bad, cudaStream_t s);
+// Polar orthonormalisation helpers (m x m, leading dimension m): Y = G - I in place with fro2[0] = ||Y||_F^2;
+// Z = a Y + b I; Z += b I.
+cudaError_t eye_residual(double* G, int m, double* fro2, cudaStream_t s);
+cudaError_t scaled_plus_identity(const double* Y, int m, double a, double b, double* Z, cudaStream_t s);
+cudaError_t add_diag(double* Z, int m, double b, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------------------- sub-blocks
 struct BlockArgs {

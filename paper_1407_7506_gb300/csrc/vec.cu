@@ -150,9 +150,63 @@ __global__ void check_finite_kernel(const double* __restrict__ v, int m, int* ba
     if (!isfinite(v[i])) atomicAdd(bad, 1);
 }
 
+// Y = G - I in place (m x m, leading dimension m) and out[0] = ||Y||_F^2 (one CTA, fixed summation order).
+__global__ void __launch_bounds__(1024) eye_residual_kernel(double* G, int m, double* out) {
+  double acc = 0.0;
+  for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    const double y = G[e] - (i == j ? 1.0 : 0.0);
+    G[e] = y;
+    acc = fma(y, y, acc);
+  }
+  __shared__ double red[1024];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
+// Z = a Y + b I (m x m)
+__global__ void scaled_plus_identity_kernel(const double* __restrict__ Y, int m, double a, double b, double* Z) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)m * m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    Z[e] = a * Y[e] + (i == j ? b : 0.0);
+  }
+}
+
+__global__ void add_diag_kernel(double* Z, int m, double b) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) Z[i + (int64_t)i * m] += b;
+}
+
 }  // namespace
 
 int64_t norm_row_tiles(int64_t n) { return ceil_div(n, kRows); }
+
+cudaError_t eye_residual(double* G, int m, double* fro2, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  eye_residual_kernel<<<1, 1024, 0, s>>>(G, m, fro2);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t scaled_plus_identity(const double* Y, int m, double a, double b, double* Z, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  const int64_t blocks = ceil_div((int64_t)m * m, 256);
+  scaled_plus_identity_kernel<<<(unsigned)(blocks < 1024 ? blocks : 1024), 256, 0, s>>>(Y, m, a, b, Z);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t add_diag(double* Z, int m, double b, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  add_diag_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(Z, m, b);
+  count_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t residual_diag(const double* X, const double* HX, int64_t ld, int64_t n, int m, const double* lam,
                           const ResidualArgs& ra, double* W, cudaStream_t s) {

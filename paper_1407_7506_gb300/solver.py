@@ -25,7 +25,8 @@ class Solver:
     """
 
     def __init__(self, V, grid, k, sbsize, rr_period=5, h=1.0, nbuf=0, maxiter=0, lock=True, timing=False,
-                 sigma_floor=0.0, device="cuda", stream=None, history=0, precision="fp64", fp64_gemm="fma"):
+                 sigma_floor=0.0, device="cuda", stream=None, history=0, precision="fp64", fp64_gemm="fma",
+                 orth="cholqr2", orth_skip_tol=0.0):
         if not torch.cuda.is_available():
             raise RuntimeError("the PPCG library needs a CUDA GPU; no CPU fallback exists")
         nx, ny, nz = (grid, grid, grid) if np.isscalar(grid) else tuple(grid)
@@ -44,6 +45,8 @@ class Solver:
         self.opt.sigma_floor = sigma_floor
         self.opt.precision = {"fp64": 0, "mixed_tf32": 1, "mixed": 1}[precision]
         self.opt.fp64_gemm = {"fma": 0, "ozaki": 1}[fp64_gemm]
+        self.opt.orth = {"cholqr2": 0, "polar": 1}[orth]
+        self.opt.orth_skip_tol = orth_skip_tol
         self._hist = np.zeros(4 * max(history, 1))
         if history:
             self.opt.history_cap = history

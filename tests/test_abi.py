@@ -87,6 +87,16 @@ def test_argument_validation(lib, n, k, q, nbuf, expect):
     assert st == expect
 
 
+@pytest.mark.parametrize("field,value", [("orth", 2), ("orth", -1), ("orth_skip_tol", -1e-3),
+                                         ("orth_skip_tol", float("nan")), ("fp64_gemm", 2)])
+def test_invalid_option_values(lib, field, value):
+    opt = pk.ppcg_options()
+    setattr(opt, field, value)
+    out = ctypes.c_size_t(0)
+    assert (lib.ppcg_workspace_bytes(ctypes.byref(_op(16)), 4096, 8, 2, ctypes.byref(opt), ctypes.byref(out))
+            == pk.PPCG_ERR_ARG)
+
+
 def test_unsupported_options_are_reported(lib):
     op = _op(16)
     op.dtype = 1

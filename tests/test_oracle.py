@@ -315,6 +315,100 @@ def test_ppcg_warm_start_converges_immediately():
     assert r.converged and r.iters == 0
 
 
+# ---------------------------------------------------------------- orthonormalisation variants (Section 5.4, R10)
+def test_polar_series_sums_to_inverse_square_root():
+    # the binomial series of (1 + y)^{-1/2}, summed far out, equals the closed form at scalar y
+    c = oracle.polar_coefficients(60)
+    for y in (-0.3, -0.01, 0.02, 0.4):
+        assert abs(np.polyval(c[::-1], y) - 1.0 / np.sqrt(1.0 + y)) < 1e-14
+
+
+def test_polar_terms_rule():
+    u = np.finfo(np.float64).eps / 2
+    c = oracle.polar_coefficients(oracle.POLAR_MAX_TERMS + 1)
+    assert oracle.polar_terms(0.0) == 1 and oracle.polar_terms(1e-12) == 1
+    assert oracle.polar_terms(0.2) is None
+    for nu in (1e-8, 1e-5, 1e-3, 1e-2):
+        t = oracle.polar_terms(nu)
+        assert abs(c[t + 1]) * nu ** (t + 1) <= u                 # first omitted term below roundoff
+        assert t == 1 or abs(c[t]) * nu ** t > u                  # and t is the fewest such
+
+
+@pytest.mark.parametrize("nu", [1e-9, 1e-5, 1e-2])
+def test_orth_polar_equals_svd_polar_factor(nu):
+    # X = Q (I + E) with E symmetric, ||X*X - I|| ~ nu: the series result is the orthonormal polar factor of X,
+    # computed independently from the SVD (scipy.linalg.polar), to FP64 accuracy
+    n, m = 300, 12
+    rng = _rng(int(-np.log10(nu)))
+    Q = sla.qr(rng.standard_normal((n, m)), mode="economic")[0]
+    E = rng.standard_normal((m, m))
+    E = 0.5 * (E + E.T)
+    E *= 0.5 * nu / np.linalg.norm(E)
+    Z = rng.standard_normal((m, m))
+    X = Q @ (np.eye(m) + E) @ sla.expm(1e-1 * (Z - Z.T))
+    t = oracle.polar_terms(np.linalg.norm(X.T @ X - np.eye(m)))
+    U = oracle.orth_polar(X, t)
+    Up, Hp = sla.polar(X)
+    np.testing.assert_allclose(U, Up, atol=5e-15)
+    np.testing.assert_allclose(U.T @ U, np.eye(m), atol=5e-15)
+
+
+def test_orth_polar_of_scaled_orthonormal_columns_is_exact():
+    # X = Q diag(s): X*X = diag(s^2) and the polar factor is Q
+    n, m = 200, 6
+    rng = _rng(3)
+    Q = sla.qr(rng.standard_normal((n, m)), mode="economic")[0]
+    s = 1.0 + 1e-4 * rng.standard_normal(m)
+    X = Q * s[None, :]
+    U = oracle.orth_polar(X, oracle.polar_terms(np.linalg.norm(s ** 2 - 1.0)))
+    np.testing.assert_allclose(U, Q, atol=2e-15)
+
+
+def test_orthonormalize_skip_and_fallback():
+    n, m = 200, 5
+    rng = _rng(4)
+    Q = sla.qr(rng.standard_normal((n, m)), mode="economic")[0]
+    st = {"n_orth_skip": 0, "n_polar": 0, "n_cholqr_fallback": 0}
+    assert oracle.orthonormalize(Q, "cholqr2", 1e-10, st) is Q and st["n_orth_skip"] == 1
+    X = rng.standard_normal((n, m))                          # far from orthonormal: the series is not used
+    U = oracle.orthonormalize(X, "polar", 0.0, st)
+    assert st["n_polar"] == 0
+    np.testing.assert_allclose(U, oracle.cholqr2(X)[0], atol=1e-14)
+
+
+@pytest.mark.parametrize("mode,skip", [("polar", 0.0), ("cholqr2", 1e-14), ("polar", 1e-3)])
+def test_ppcg_orth_variants_match_dense_eigh(mode, skip):
+    N, k = 7, 10
+    w = wl.small("orthv", N=N, k=k, sbsize=2, seed=61)
+    V, X0 = wl.make_inputs(w)
+    ev = np.linalg.eigvalsh(oracle.assemble_H(V, N, 1.0))[:k]
+    r = oracle.ppcg(V, N, 1.0, k, 2, 5, X0, tol=1e-8, maxiter=2000, orth_mode=mode, orth_skip_tol=skip)
+    assert r.converged and np.max(r.res) <= 1e-8
+    np.testing.assert_allclose(r.lam, ev, rtol=0, atol=1e-10)
+    np.testing.assert_allclose(r.X.T @ r.X, np.eye(k), atol=1e-12)
+    assert r.stats["n_polar"] + r.stats["n_orth_skip"] > 0
+
+
+def test_planted_polar_sign_error_is_caught():
+    real = oracle.ppcg.__globals__["polar_coefficients"]
+
+    def wrong(t):
+        c = real(t)
+        c[1] = -c[1]
+        return c
+    n, m = 200, 6
+    rng = _rng(8)
+    Q = sla.qr(rng.standard_normal((n, m)), mode="economic")[0]
+    X = Q @ (np.eye(m) + 1e-3 * np.diag(rng.standard_normal(m)))
+    t = oracle.polar_terms(np.linalg.norm(X.T @ X - np.eye(m)))
+    oracle.ppcg.__globals__["polar_coefficients"] = wrong
+    try:
+        U = oracle.orth_polar(X, t)
+    finally:
+        oracle.ppcg.__globals__["polar_coefficients"] = real
+    assert np.max(np.abs(U - sla.polar(X)[0])) > 1e-6
+
+
 # ---------------------------------------------------------------- planted mistakes are caught
 def test_planted_stencil_sign_error_is_caught():
     real = oracle.apply_H

@@ -26,9 +26,9 @@ def _gpu():
 
 
 def _gpu_solve(V, N, k, q, rr, X0, tol=1e-8, nbuf=0, lock=True, maxiter=3000, history=0, precision="fp64",
-               fp64_gemm="fma"):
+               fp64_gemm="fma", orth="cholqr2", orth_skip_tol=0.0):
     s = pk.Solver(V, N, k, q, rr_period=rr, nbuf=nbuf, lock=lock, maxiter=maxiter, history=history,
-                  precision=precision, fp64_gemm=fp64_gemm)
+                  precision=precision, fp64_gemm=fp64_gemm, orth=orth, orth_skip_tol=orth_skip_tol)
     try:
         lam, X, res, st = s.solve(X0, tol)
         return lam, X.cpu().numpy().T.copy(), res, st
@@ -151,6 +151,41 @@ def test_fp64_emulation_solve_config1(precision):
     assert st["converged"] == 1, st
     assert np.all(_rel(lam, gold) <= (LAM_TOL if precision == "fp64" else LAM_TOL_MIXED)), np.max(_rel(lam, gold))
     _check_pairs(V, w.N, lam, X, w.tol)
+
+
+# ---------------------------------------------------------------- orthonormalisation variants (Section 5.4)
+@pytest.mark.parametrize("orth,skip,precision,gemm", [
+    ("polar", 0.0, "fp64", "fma"),
+    ("cholqr2", 1e-14, "fp64", "fma"),
+    ("polar", 1e-3, "fp64", "fma"),
+    ("polar", 0.0, "mixed", "ozaki"),
+])
+def test_orth_variants_solve(orth, skip, precision, gemm):
+    N, k, q = 8, 10, 2
+    w = wl.small("orthv", N=N, k=k, sbsize=q, seed=77)
+    V, X0 = wl.make_inputs(w)
+    lam, X, res, st = _gpu_solve(V, N, k, q, 5, X0, precision=precision, fp64_gemm=gemm, orth=orth,
+                                 orth_skip_tol=skip)
+    assert st["status"] == "ok" and st["converged"] == 1
+    assert st["n_polar"] + st["n_orth_skip"] > 0
+    if orth == "cholqr2":
+        assert st["n_polar"] == 0
+    _check_pairs(V, N, lam, X, 1e-8)
+    ev = np.linalg.eigvalsh(oracle.assemble_H(V, N, 1.0))[:k]
+    assert np.all(_rel(lam, ev) <= (LAM_TOL if precision == "fp64" else 1e-9))
+    ref = oracle.ppcg(V, N, 1.0, k, q, 5, X0, tol=1e-8, maxiter=3000, orth_mode=orth, orth_skip_tol=skip)
+    assert ref.converged and np.all(_rel(lam, ref.lam) <= 1e-9)
+    assert st["iters"] <= 2 * ref.iters + 50, (st["iters"], ref.iters)
+
+
+def test_polar_form_config1_against_dense_golden():
+    w = wl.CONFIGS[1]
+    V, X0 = wl.make_inputs(w)
+    gold = np.loadtxt(os.path.join(GOLDEN, "config1_dense_eigs.txt"))
+    lam, X, res, st = _gpu_solve(V, w.N, w.k, w.sbsize, w.rr_period, X0, orth="polar")
+    assert st["status"] == "ok" and st["converged"] == 1 and st["n_polar"] > 0
+    assert np.all(_rel(lam, gold[:w.k]) <= LAM_TOL)
+    _check_pairs(V, w.N, lam, X, 1e-8)
 
 
 def test_solve_k1():
