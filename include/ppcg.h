@@ -149,6 +149,46 @@ PPCG_API ppcg_status ppcg_solve(ppcg_handle h, const double* X0, double tol, dou
 /* Release the handle (and the workspace if the library allocated it). NULL is accepted. */
 PPCG_API ppcg_status ppcg_destroy(ppcg_handle h);
 
+/*
+ * Many independent eigenproblems (uneven n and k, each with its own handle) solved concurrently, for workloads
+ * of many small Hamiltonians such as the per-k-point or per-system solves around Section 6. Each item is one
+ * ppcg_solve call; the library runs up to max_concurrent of them at once on native threads, each on its own
+ * handle's stream (give every handle its own stream, or they serialise). Cooperative grid-barrier kernels of
+ * different items are ordered one after another on the device; everything else overlaps.
+ *   items           count entries; h, X0, tol, lambda, X, resnorm, stats as in ppcg_solve (stats may be NULL);
+ *                   status and time_ms are written per item (time_ms: host wall time of that solve)
+ *   max_concurrent  <= 0 means min(count, 16)
+ * Returns PPCG_OK when every item returned PPCG_OK, otherwise the first non-OK item status in item order
+ * (PPCG_ERR_ARG for a NULL items array, a NULL handle or count < 0). Items must use distinct handles.
+ */
+typedef struct {
+  ppcg_handle h;
+  const double* X0;
+  double tol;
+  double* lambda;
+  double* X;
+  double* resnorm;
+  ppcg_stats* stats;
+  int32_t status;     /* out: ppcg_status of this item's solve */
+  int32_t reserved;
+  double time_ms;     /* out */
+} ppcg_batch_item;
+
+PPCG_API ppcg_status ppcg_solve_batched(ppcg_batch_item* items, int32_t count, int32_t max_concurrent);
+
+/*
+ * Autotuner for the sub-block size q (Section 5.1; the paper's sbsize experiments in Section 7 show that the
+ * best q depends on the problem). For each candidate q in candidates[0..ncand) with 1 <= q <= min(k + nbuf, 16)
+ * it creates a solver (library-allocated workspace), solves from X0 to tol on cuda_stream and times the solve
+ * with CUDA events; time_ms[i] receives the time (a negative value for a candidate that was invalid or did not
+ * converge) and *best the fastest converged q. Returns PPCG_OK if at least one candidate converged, else the
+ * status of the last candidate tried.
+ */
+PPCG_API ppcg_status ppcg_autotune_sbsize(const ppcg_operator* op, int64_t n, int32_t k, int32_t rr_period,
+                                          const ppcg_options* opt, const double* X0, double tol,
+                                          const int32_t* candidates, int32_t ncand, void* cuda_stream,
+                                          int32_t* best, double* time_ms);
+
 #ifdef __cplusplus
 }
 #endif

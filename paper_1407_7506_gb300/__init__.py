@@ -27,7 +27,7 @@ PHASES = ("AX", "GEMM", "BlockRR", "CholQR", "RR", "Precond", "Lock", "Other")
 EXPORTS = ("ppcg_status_string", "ppcg_workspace_bytes", "ppcg_create", "ppcg_set_potential", "ppcg_solve",
            "ppcg_destroy", "ppcg_apply_operator", "ppcg_gram", "ppcg_project", "ppcg_cholqr2", "ppcg_dense_eigh",
            "ppcg_block_coefficients", "ppcg_block_update", "ppcg_residual", "ppcg_gram_noalloc",
-           "ppcg_energy_gradient")
+           "ppcg_energy_gradient", "ppcg_solve_batched", "ppcg_autotune_sbsize")
 
 
 class ppcg_operator(ctypes.Structure):
@@ -54,6 +54,13 @@ class ppcg_stats(ctypes.Structure):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "t_phase_ms"}
         d["t_phase_ms"] = dict(zip(PHASES, list(self.t_phase_ms)))
         return d
+
+
+class ppcg_batch_item(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_void_p), ("X0", ctypes.c_void_p), ("tol", ctypes.c_double),
+                ("lam", ctypes.c_void_p), ("X", ctypes.c_void_p), ("resnorm", ctypes.c_void_p),
+                ("stats", ctypes.POINTER(ppcg_stats)), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("time_ms", ctypes.c_double)]
 
 
 class PPCGError(RuntimeError):
@@ -92,6 +99,9 @@ def lib():
             "ppcg_residual": (_i32, [_vp, _vp, _vp, _i64, _i32, _vp, _vp, _d, _vp, _vp]),
             "ppcg_gram_noalloc": (_i32, [_vp, _i64, _vp, _i64, _i64, _i32, _i32, _vp, _vp]),
             "ppcg_energy_gradient": (_i32, [_vp, _vp, _i64, _i32, _d, _vp]),
+            "ppcg_solve_batched": (_i32, [P(ppcg_batch_item), _i32, _i32]),
+            "ppcg_autotune_sbsize": (_i32, [P(ppcg_operator), _i64, _i32, _i32, P(ppcg_options), _vp, _d,
+                                            P(_i32), _i32, _vp, P(_i32), P(_d)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -185,5 +195,27 @@ def ppcg_gram_noalloc(A, lda, B, ldb, n, ma, mb, C, stream=0):
     _check(lib().ppcg_gram_noalloc(A, lda, B, ldb, n, ma, mb, C, stream), "ppcg_gram_noalloc")
 
 
-from .solver import Solver  # noqa: E402,F401
+
+
+def ppcg_solve_batched(items, max_concurrent=0):
+    """items: a ctypes array of ppcg_batch_item. Returns the batch status (PPCG_OK or PPCG_ERR_NOT_CONVERGED);
+    other statuses raise. Per-item status and time_ms are written into the items."""
+    st = lib().ppcg_solve_batched(items, len(items), max_concurrent)
+    if st not in (PPCG_OK, PPCG_ERR_NOT_CONVERGED):
+        raise PPCGError(st, "ppcg_solve_batched")
+    return st
+
+
+def ppcg_autotune_sbsize(op, n, k, rr_period, opt, X0_ptr, tol, candidates, stream=0):
+    """Returns (best sbsize, list of per-candidate times in ms, negative where invalid or not converged)."""
+    cand = (_i32 * len(candidates))(*candidates)
+    times = (_d * len(candidates))()
+    best = _i32(0)
+    _check(lib().ppcg_autotune_sbsize(ctypes.byref(op), n, k, rr_period, ctypes.byref(opt) if opt else None, X0_ptr,
+                                      tol, cand, len(candidates), stream, ctypes.byref(best), times),
+           "ppcg_autotune_sbsize")
+    return best.value, list(times)
+
+
+from .solver import Solver, BatchSolver  # noqa: E402,F401
 from .autograd import smallest_eigsum  # noqa: E402,F401

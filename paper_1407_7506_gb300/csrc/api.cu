@@ -16,9 +16,11 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 using namespace ppcg;
@@ -871,3 +873,76 @@ ppcg_status ppcg_energy_gradient(ppcg_handle c, const double* X, int64_t ld, int
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------ batched solves
+extern "C" ppcg_status ppcg_solve_batched(ppcg_batch_item* items, int32_t count, int32_t max_concurrent) {
+  if (!items || count < 0) return PPCG_ERR_ARG;
+  for (int i = 0; i < count; ++i)
+    if (!items[i].h) return PPCG_ERR_ARG;
+  if (count == 0) return PPCG_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PPCG_ERR_CUDA;
+  int workers = max_concurrent > 0 ? max_concurrent : 16;
+  if (workers > count) workers = count;
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    cudaSetDevice(dev);
+    for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) {
+      ppcg_batch_item& it = items[i];
+      const auto t0 = std::chrono::steady_clock::now();
+      it.status = ppcg_solve(it.h, it.X0, it.tol, it.lambda, it.X, it.resnorm, it.stats);
+      it.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+  };
+  std::vector<std::thread> pool;
+  pool.reserve(workers > 1 ? workers - 1 : 0);
+  for (int w = 1; w < workers; ++w) pool.emplace_back(work);
+  work();
+  for (auto& t : pool) t.join();
+  for (int i = 0; i < count; ++i)
+    if (items[i].status != PPCG_OK) return (ppcg_status)items[i].status;
+  return PPCG_OK;
+}
+
+extern "C" ppcg_status ppcg_autotune_sbsize(const ppcg_operator* op, int64_t n, int32_t k, int32_t rr_period,
+                                            const ppcg_options* opt, const double* X0, double tol,
+                                            const int32_t* candidates, int32_t ncand, void* cuda_stream,
+                                            int32_t* best, double* time_ms) {
+  if (!op || !X0 || !candidates || ncand < 1 || !best || !(tol > 0.0)) return PPCG_ERR_ARG;
+  const int nbuf = opt ? opt->nbuf : 0;
+  std::vector<double> lam((size_t)k), res((size_t)k);
+  double* Xout = nullptr;
+  if (cudaMalloc(&Xout, sizeof(double) * (size_t)n * k) != cudaSuccess) return PPCG_ERR_OOM;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  ppcg_status last = PPCG_ERR_ARG;
+  double best_ms = -1.0;
+  *best = 0;
+  for (int i = 0; i < ncand; ++i) {
+    const int q = candidates[i];
+    if (time_ms) time_ms[i] = -1.0;
+    if (q < 1 || q > kMaxSbsize || q > k + nbuf) continue;
+    ppcg_handle h = nullptr;
+    last = ppcg_create(op, n, k, q, rr_period, opt, cuda_stream, nullptr, 0, &h);
+    if (last != PPCG_OK) continue;
+    cudaEventRecord(e0, s);
+    last = ppcg_solve(h, X0, tol, lam.data(), Xout, res.data(), nullptr);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ppcg_destroy(h);
+    if (last != PPCG_OK) continue;
+    if (time_ms) time_ms[i] = ms;
+    if (best_ms < 0.0 || ms < best_ms) {
+      best_ms = ms;
+      *best = q;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(Xout);
+  return best_ms >= 0.0 ? PPCG_OK : last;
+}

@@ -13,6 +13,7 @@
 
 #include <cmath>
 #include <math_constants.h>
+#include <mutex>
 
 namespace ppcg {
 
@@ -467,20 +468,51 @@ struct CoopLimit {
   int chol = 0, jac = 0;
 };
 
-CoopLimit& coop_limits() {
-  static CoopLimit lim;
-  if (lim.chol == 0) {
+const CoopLimit& coop_limits() {
+  static const CoopLimit lim = [] {          // initialised once, thread-safe (concurrent batched solves)
+    CoopLimit l;
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int per = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, chol_inv_kernel, 256, 0);
-    lim.chol = (per > 0 ? per : 1) * sms;
+    l.chol = (per > 0 ? per : 1) * sms;
     per = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, jacobi_kernel, 256, 0);
-    lim.jac = (per > 0 ? per : 1) * sms;
-  }
+    l.jac = (per > 0 ? per : 1) * sms;
+    return l;
+  }();
   return lim;
+}
+
+// Cooperative launches from several streams (concurrent solves) are chained: each waits on the event recorded
+// after the previous one, so two grid-barrier kernels are never resident together and waiting on each other's
+// SMs. The chain only points back to earlier launches, so it cannot form a cycle.
+constexpr int kMaxCoopDevices = 64;
+std::mutex g_coop_mu;
+cudaEvent_t g_coop_ev[kMaxCoopDevices] = {};
+bool g_coop_any[kMaxCoopDevices] = {};
+
+cudaError_t coop_launch(const void* fn, unsigned grid, void** args, cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxCoopDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_coop_mu);
+  if (!g_coop_ev[dev]) {
+    e = cudaEventCreateWithFlags(&g_coop_ev[dev], cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  if (g_coop_any[dev]) {
+    e = cudaStreamWaitEvent(s, g_coop_ev[dev], 0);
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, 0, s);
+  if (e != cudaSuccess) return e;
+  e = cudaEventRecord(g_coop_ev[dev], s);
+  if (e != cudaSuccess) return e;
+  g_coop_any[dev] = true;
+  return cudaSuccess;
 }
 
 inline int pad_tile(int m) { return (int)ceil_div(m, TB) * TB; }
@@ -513,7 +545,7 @@ cudaError_t chol_inv(const double* G, int m, double shift, double* Rinv, double*
   void* args[] = {(void*)&G, (void*)&m, (void*)&mp, (void*)&shift, (void*)&Rinv, (void*)&Lw,
                   (void*)&Linv, (void*)&Lp, (void*)&diag0, (void*)&flag, (void*)&bar};
   count_launch();
-  return cudaLaunchCooperativeKernel((const void*)chol_inv_kernel, dim3(grid), dim3(256), args, 0, s);
+  return coop_launch((const void*)chol_inv_kernel, (unsigned)grid, args, s);
 }
 
 size_t jacobi_ws_elems(int m) {
@@ -555,7 +587,7 @@ cudaError_t jacobi_eigh(const double* M, int m, double* lambda, double* C, doubl
   void* args[] = {(void*)&jb, (void*)&m, (void*)&mp, (void*)&nrm_c, (void*)&counts, (void*)&flag, (void*)&bar,
                   (void*)&info};
   count_launch();
-  e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(grid), dim3(256), args, 0, s);
+  e = coop_launch((const void*)jacobi_kernel, (unsigned)grid, args, s);
   if (e != cudaSuccess) return e;
   jacobi_sort_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(jb, m, mp, info, lambda, perm);
   count_launch();

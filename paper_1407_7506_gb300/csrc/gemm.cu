@@ -228,13 +228,12 @@ small_gemm_kernel(const double* __restrict__ A, int64_t lda, const double* __res
 }
 
 int grid_sm_count() {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
+  static const int sms = [] {               // initialised once, thread-safe (concurrent batched solves)
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
   return sms;
 }
 

@@ -337,13 +337,12 @@ cudaError_t set_smem(const void* fn, size_t& bytes, int NT) {
 }
 
 int sm_count() {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
+  static const int sms = [] {               // initialised once, thread-safe (concurrent batched solves)
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
   return sms;
 }
 

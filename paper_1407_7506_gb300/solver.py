@@ -9,8 +9,8 @@ import ctypes
 import numpy as np
 import torch
 
-from . import (PPCG_ERR_NOT_CONVERGED, PPCG_OK, ppcg_create, ppcg_destroy, ppcg_operator, ppcg_options, ppcg_solve,
-               ppcg_stats, ppcg_workspace_bytes, ppcg_set_potential)
+from . import (PPCG_ERR_NOT_CONVERGED, PPCG_OK, ppcg_batch_item, ppcg_create, ppcg_destroy, ppcg_operator,
+               ppcg_options, ppcg_solve, ppcg_solve_batched, ppcg_stats, ppcg_workspace_bytes, ppcg_set_potential)
 
 
 def _ptr(t):
@@ -89,3 +89,62 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def _status_name(status):
+    return "ok" if status == PPCG_OK else ("not_converged" if status == PPCG_ERR_NOT_CONVERGED else status)
+
+
+class BatchSolver:
+    """Independent problems of uneven size solved concurrently through ppcg_solve_batched.
+
+    problems: list of dicts with keys V, grid, k, sbsize and optionally rr_period. Each problem gets its own
+    Solver (handle, workspace) on its own CUDA stream; solver_kw are passed to every Solver.
+    """
+
+    def __init__(self, problems, device="cuda", **solver_kw):
+        self.device = torch.device(device)
+        self.solvers = []
+        for p in problems:
+            st = torch.cuda.Stream(device=self.device)
+            with torch.cuda.stream(st):
+                self.solvers.append(Solver(p["V"], p["grid"], p["k"], p["sbsize"], rr_period=p.get("rr_period", 5),
+                                           device=device, stream=st, **solver_kw))
+
+    def solve(self, X0s, tol=1e-8, max_concurrent=0):
+        """X0s: one start block per problem (as for Solver.solve). Returns (results, batch_status): results is a
+        list of (lam, X, res, stats) with stats["time_ms"] the problem's own wall time."""
+        n = len(self.solvers)
+        items = (ppcg_batch_item * n)()
+        keep = []
+        for i, (s, X0) in enumerate(zip(self.solvers, X0s)):
+            with torch.cuda.stream(s.stream):
+                if isinstance(X0, np.ndarray):
+                    X0t = torch.from_numpy(np.ascontiguousarray(X0.T)).to(self.device)
+                else:
+                    X0t = X0
+                X = torch.empty((s.k, s.n), dtype=torch.float64, device=self.device)
+            assert X0t.shape == (s.k + s.nbuf, s.n) and X0t.dtype == torch.float64 and X0t.is_contiguous()
+            lam, res, st = np.zeros(s.k), np.zeros(s.k), ppcg_stats()
+            items[i].h = s.handle
+            items[i].X0 = X0t.data_ptr()
+            items[i].tol = tol
+            items[i].lam = lam.ctypes.data
+            items[i].X = X.data_ptr()
+            items[i].resnorm = res.ctypes.data
+            items[i].stats = ctypes.pointer(st)
+            keep.append((X0t, X, lam, res, st))
+        for s in self.solvers:
+            s.stream.synchronize()                       # start blocks are on the device before the solves run
+        status = ppcg_solve_batched(items, max_concurrent)
+        out = []
+        for i, (X0t, X, lam, res, st) in enumerate(keep):
+            d = st.as_dict()
+            d["status"] = _status_name(items[i].status)
+            d["time_ms"] = items[i].time_ms
+            out.append((lam, X, res, d))
+        return out, _status_name(status)
+
+    def close(self):
+        for s in self.solvers:
+            s.close()

@@ -29,7 +29,7 @@ def _declared():
 
 def test_exports_match_headers(lib):
     declared = _declared()
-    assert len(declared) == 16
+    assert len(declared) == 18
     assert sorted(declared) == sorted(pk.EXPORTS)
     out = subprocess.run(["nm", "-D", "--defined-only", pk.LIB_PATH], capture_output=True, text=True).stdout
     exported = set(re.findall(r"\bT (ppcg_\w+)", out))
@@ -38,16 +38,22 @@ def test_exports_match_headers(lib):
 
 
 def test_struct_layouts_match_c(tmp_path):
+    # every field offset and every struct size of the ctypes mirrors against the C compiler's
+    structs = [pk.ppcg_operator, pk.ppcg_options, pk.ppcg_stats, pk.ppcg_batch_item]
+    cnames = {"lam": "lambda"}                                  # a Python keyword in C
+    lines, want = [], []
+    for st in structs:
+        lines.append(f'printf("%zu\\n", sizeof({st.__name__}));')
+        want.append(ctypes.sizeof(st))
+        for f, _ in st._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({st.__name__}, {cnames.get(f, f)}));')
+            want.append(getattr(st, f).offset)
     src = tmp_path / "sz.c"
-    src.write_text('#include "ppcg.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(ppcg_operator), sizeof(ppcg_options),'
-                   ' sizeof(ppcg_stats), offsetof(ppcg_operator, V), offsetof(ppcg_options, sigma_floor),'
-                   ' offsetof(ppcg_stats, t_phase_ms)); return 0;}\n')
+    src.write_text('#include "ppcg.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(void){' + "".join(lines)
+                   + " return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
-    want = [ctypes.sizeof(pk.ppcg_operator), ctypes.sizeof(pk.ppcg_options), ctypes.sizeof(pk.ppcg_stats),
-            pk.ppcg_operator.V.offset, pk.ppcg_options.sigma_floor.offset, pk.ppcg_stats.t_phase_ms.offset]
     assert got == want
 
 
@@ -126,3 +132,14 @@ def test_create_without_gpu_fails_cleanly(lib):
     h = ctypes.c_void_p(0)
     st = lib.ppcg_create(ctypes.byref(op), 4096, 8, 2, 5, None, None, None, 0, ctypes.byref(h))
     assert st == pk.PPCG_ERR_CUDA and not h.value
+
+
+def test_batched_and_autotune_validate_arguments(lib):
+    assert lib.ppcg_solve_batched(None, 1, 0) == pk.PPCG_ERR_ARG
+    items = (pk.ppcg_batch_item * 2)()
+    assert lib.ppcg_solve_batched(items, 2, 0) == pk.PPCG_ERR_ARG       # NULL handles
+    assert lib.ppcg_solve_batched(items, -1, 0) == pk.PPCG_ERR_ARG
+    assert lib.ppcg_solve_batched(items, 0, 0) == pk.PPCG_OK
+    best = ctypes.c_int32(0)
+    assert lib.ppcg_autotune_sbsize(None, 4096, 8, 5, None, None, 1e-8, None, 0, None, ctypes.byref(best),
+                                    None) == pk.PPCG_ERR_ARG

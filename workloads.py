@@ -16,6 +16,10 @@ Recipes (seed = 1000 + config index, numpy default_rng; draw order: V, then X0):
   separable    V(i, j, l) = V1(i) + V2(j) + V3(l), each V_d ~ U[0, 1)  (test-only recipe)
   zero         V = 0                                                  (test-only recipe)
 X0 = standard_normal((n, k)) laid out column-major (real); complex X0 = real + 1j*imag from two draws.
+
+The batched workload (config 4) is a list of independent problems: from default_rng(1004) draw the 64 grid
+sizes N_i ~ U{12..28} and then the 64 block sizes k_i ~ U{32..256}; problem i then draws V_i ~ U[0, 1) and its
+X0_i from default_rng(1004 * 1000 + i) (V first, then X0).
 """
 from __future__ import annotations
 
@@ -54,6 +58,21 @@ CONFIGS = {
     5: Workload("grid64_k2048_q8_wells64_bloch", N=64, k=2048, sbsize=8, potential="wells", n_wells=64,
                 seed=1005, dtype="c128", theta=(0.3, 0.7, 1.1)),
 }
+
+
+def batch(count: int = 64, seed: int = 1004, n_range=(12, 28), k_range=(32, 256), sbsize: int = 4):
+    """The batched workload: `count` independent uniform-potential problems of uneven size (config 4 with the
+    defaults). Returns a list of Workloads; make_inputs(w) draws each problem's V and X0 from its own seed."""
+    rng = np.random.default_rng(seed)
+    Ns = rng.integers(n_range[0], n_range[1] + 1, size=count)
+    ks = rng.integers(k_range[0], k_range[1] + 1, size=count)
+    out = []
+    for i in range(count):
+        N, k = int(Ns[i]), int(ks[i])
+        k = min(k, N ** 3 // 2)
+        out.append(Workload(f"batch{seed}_{i}_grid{N}_k{k}", N=N, k=k, sbsize=min(sbsize, k), potential="uniform",
+                            seed=seed * 1000 + i))
+    return out
 
 
 def potential(w: Workload, rng: np.random.Generator) -> np.ndarray:
