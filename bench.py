@@ -209,6 +209,8 @@ def main():
     ap.add_argument("--forms", default="fp64,mixed,fp64_ozaki,mixed_ozaki,mixed_ozaki_polar",
                     help="forms to time; the first is the headline value (" + ", ".join(FORMS) + ")")
     ap.add_argument("--batch-concurrency", type=int, default=16, help="concurrent solves of the batched workload")
+    ap.add_argument("--batch-gemm", default="fma", choices=["fma", "ozaki"],
+                    help="FP64 GEMMs of the batched workload: FP64 FMA pipe or Ozaki emulation on tcgen05")
     args = ap.parse_args()
     if args.workload == "4":
         if args.impl == "reference":
@@ -375,6 +377,7 @@ def run_batched(args):
         op = pk.ppcg_operator(w.N, w.N, w.N, 1.0, Vd.data_ptr(), (ctypes.c_double * 3)(0.0, 0.0, 0.0), 0)
         opt = pk.ppcg_options()
         opt.maxiter = args.maxiter
+        opt.fp64_gemm = 1 if args.batch_gemm == "ozaki" else 0
         best, times = pk.ppcg_autotune_sbsize(op, w.n, w.k, w.rr_period, opt, X0d.data_ptr(), w.tol, cands,
                                               torch.cuda.current_stream(dev).cuda_stream)
         tuned[name] = best
@@ -386,7 +389,7 @@ def run_batched(args):
         problems.append({"V": V, "grid": w.N, "k": w.k, "sbsize": min(q, w.k), "rr_period": w.rr_period})
     X0s = [torch.from_numpy(np.ascontiguousarray(X0.T)).to(dev) for _, X0 in inputs]   # resident in HBM
     torch.cuda.synchronize()
-    bs = pk.BatchSolver(problems, device=dev, maxiter=args.maxiter)
+    bs = pk.BatchSolver(problems, device=dev, maxiter=args.maxiter, fp64_gemm=args.batch_gemm)
     for _ in range(args.warmup):
         bs.solve(X0s, tol=1e-8, max_concurrent=args.batch_concurrency)
     clk = ClockSampler(local)
@@ -425,7 +428,8 @@ def run_batched(args):
         "config": {"workload": "batch64_grid12-28_k32-256_uniform", "problems": len(ws),
                    "n_range": [min(w.n for w in ws), max(w.n for w in ws)],
                    "k_range": [min(w.k for w in ws), max(w.k for w in ws)], "sbsize": tuned,
-                   "concurrency": args.batch_concurrency, "l2": "per-problem working sets 2-45 MB; no flush"},
+                   "concurrency": args.batch_concurrency, "fp64_gemm": args.batch_gemm,
+                   "l2": "per-problem working sets 2-45 MB; no flush"},
         "per_problem_s": {"min": min(per), "median": statistics.median(per), "max": max(per),
                           "all": [round(x, 4) for x in per]},
         "iters": {"min": min(iters), "median": statistics.median(iters), "max": max(iters)},

@@ -55,7 +55,10 @@ typedef struct {
   double h;
   const double* V;
   double theta[3];
-  int32_t dtype; /* ppcg_dtype; this build supports PPCG_R64 */
+  int32_t dtype; /* ppcg_dtype: PPCG_R64 (theta must be 0) or PPCG_C128 (complex Hermitian, Bloch twist theta);
+                    a C128 problem is solved in its real form [[Re A, -Im A], [Im A, Re A]] of order 2n, whose
+                    eigenvalues are those of A, each twice; X0 and X are then complex (interleaved re/im), and
+                    the step entry points of ppcg_steps.h work on real-form blocks of 2n rows */
 } ppcg_operator;
 
 /* Options; a zero-initialised struct gives the defaults in brackets. */
@@ -115,7 +118,7 @@ PPCG_API ppcg_status ppcg_workspace_bytes(const ppcg_operator* op, int64_t n, in
  * Create a solver for the k smallest eigenpairs of op (Algorithm 3 inputs: A, T, rr_period, sbsize, nbuf).
  *   n           must equal nx*ny*nz
  *   k           1 <= k, k + nbuf <= n/2
- *   sbsize      sub-block size q of Section 5.1, 1 <= sbsize <= min(k + nbuf, 16)
+ *   sbsize      sub-block size q of Section 5.1, 1 <= sbsize <= min(k + nbuf, 16) (8 for PPCG_C128)
  *   rr_period   Rayleigh-Ritz period (Section 5.5), >= 1
  *   opt         may be NULL (defaults)
  *   cuda_stream a cudaStream_t (NULL = legacy default stream)
@@ -133,10 +136,11 @@ PPCG_API ppcg_status ppcg_set_potential(ppcg_handle h, const double* V);
 /*
  * Run Algorithm 3 from the starting block X0 until every one of the first k Ritz pairs has residual
  * ||A x_i - lambda_i x_i||_2 <= tol at a Rayleigh-Ritz step, or maxiter iterations.
- *   X0      n x (k + nbuf), ld = n, host or device memory (need not be orthonormal; it is orthonormalised)
+ *   X0      n x (k + nbuf), ld = n, host or device memory (need not be orthonormal; it is orthonormalised);
+ *           complex (interleaved re/im) for a PPCG_C128 operator, and so is X
  *   lambda  host, k doubles: Ritz values, ascending
  *   X       n x k, ld = n, host or device memory (may alias X0): Ritz vectors, unit norm, with the entry of
- *           largest modulus (lowest index on ties) positive
+ *           largest modulus (lowest index on ties) real positive
  *   resnorm host, k doubles: ||A x_i - lambda_i x_i||_2 recomputed on the returned pairs (may be NULL)
  *   stats   may be NULL
  * The preconditioner is T = diag(1 / max(6/h^2 + V_p - sigma, delta)), sigma the smallest Ritz value of the

@@ -65,8 +65,9 @@ PPCG_API ppcg_status ppcg_residual(ppcg_handle h, const double* X, const double*
 
 /* Adjoint of the solve with respect to the potential (Hellmann-Feynman): for E = sum_{i<k} lambda_i and
  * unit-norm eigenvectors x_i of A = -Laplacian_h + diag(V), dE/dV_p = sum_{i<k} x_i(p)^2 (the density), valid
- * when lambda_k < lambda_{k+1}. grad_V[p] = scale * sum_{c<k} X[p, c]^2 for X n x k (ld), as returned by
- * ppcg_solve; scale is the upstream gradient of E. Device pointers; grad_V has n entries. */
+ * when lambda_k < lambda_{k+1}. grad_V[p] = scale * sum_{c<k} |X[p, c]|^2 for X n x k (ld), as returned by
+ * ppcg_solve (complex, interleaved re/im with ld counted in complex entries, for a PPCG_C128 handle); scale is
+ * the upstream gradient of E. Device pointers; grad_V has n entries. */
 PPCG_API ppcg_status ppcg_energy_gradient(ppcg_handle h, const double* X, int64_t ld, int32_t k, double scale,
                                           double* grad_V);
 

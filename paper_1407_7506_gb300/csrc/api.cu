@@ -59,6 +59,9 @@ struct ppcg_ctx {
   bool ozaki = false;      // FP64 n x k GEMMs emulated on the BF16 tensor cores (error-free splitting)
   int* ozexps = nullptr;   // exponent workspace of the emulated GEMMs
   int* tcflag = nullptr;   // timeout flag of the tensor-core kernels
+  bool cplx = false;       // complex Hermitian (Bloch) problem, solved in the real form of order 2 ng
+  int64_t ng = 0;          // grid points (the complex order); n = 2 ng for a complex handle
+  int kc = 0;              // wanted complex pairs (k = 2 kc internally)
 };
 
 namespace {
@@ -141,13 +144,17 @@ ppcg_status check_args(const ppcg_operator* op, int64_t n, int32_t k, int32_t sb
   if (op->nx < 1 || op->ny < 1 || op->nz < 1 || op->nz > 65535) return PPCG_ERR_ARG;
   if ((int64_t)op->nx * op->ny * op->nz != n) return PPCG_ERR_ARG;
   if (!(op->h > 0.0) || !std::isfinite(op->h)) return PPCG_ERR_ARG;
-  if (op->dtype != PPCG_R64) return PPCG_ERR_UNSUPPORTED;
-  if (op->theta[0] != 0.0 || op->theta[1] != 0.0 || op->theta[2] != 0.0) return PPCG_ERR_UNSUPPORTED;
+  if (op->dtype != PPCG_R64 && op->dtype != PPCG_C128) return PPCG_ERR_UNSUPPORTED;
+  for (int d = 0; d < 3; ++d)
+    if (!std::isfinite(op->theta[d])) return PPCG_ERR_ARG;
+  const bool cplx = op->dtype == PPCG_C128;
+  if (!cplx && (op->theta[0] != 0.0 || op->theta[1] != 0.0 || op->theta[2] != 0.0)) return PPCG_ERR_UNSUPPORTED;
   const int nbuf = opt ? opt->nbuf : 0;
   if (k < 1 || nbuf < 0 || rr_period < 1) return PPCG_ERR_ARG;
   const int64_t kt = (int64_t)k + nbuf;
-  if (2 * kt > n || kt > 65535) return PPCG_ERR_ARG;
-  if (sbsize < 1 || sbsize > kMaxSbsize || sbsize > kt) return PPCG_ERR_ARG;
+  const int f = cplx ? 2 : 1;                    // a complex column is a pair of real-form columns
+  if (2 * kt > n || f * kt > 65535) return PPCG_ERR_ARG;
+  if (sbsize < 1 || f * sbsize > kMaxSbsize || sbsize > kt) return PPCG_ERR_ARG;
   if (opt && (opt->maxiter < 0 || opt->sigma_floor < 0.0)) return PPCG_ERR_ARG;
   if (opt && opt->precision != PPCG_FP64 && opt->precision != PPCG_MIXED_TF32) return PPCG_ERR_UNSUPPORTED;
   if (opt && (opt->fp64_gemm < 0 || opt->fp64_gemm > 1)) return PPCG_ERR_ARG;
@@ -535,7 +542,7 @@ void record(ppcg_ctx* c, ppcg_stats* S, int it, int kind, double value, double t
 double ritz_trace(const ppcg_ctx* c) {
   double t = 0.0;
   for (int i = 0; i < c->k; ++i) t += c->lam_h[i];
-  return t;
+  return c->cplx ? 0.5 * t : t;            // the real form holds every complex Ritz value twice
 }
 
 }  // namespace
@@ -568,7 +575,8 @@ ppcg_status ppcg_workspace_bytes(const ppcg_operator* op, int64_t n, int32_t k, 
   if (!bytes) return PPCG_ERR_ARG;
   PS(check_args(op, n, k, sbsize, 1, opt));
   const int kt = k + (opt ? opt->nbuf : 0);
-  *bytes = layout(make_sizes(n, kt, sbsize)).total;
+  const int f = op->dtype == PPCG_C128 ? 2 : 1;
+  *bytes = layout(make_sizes(f * n, f * kt, f * sbsize)).total;
   return PPCG_OK;
 }
 
@@ -591,14 +599,23 @@ ppcg_status ppcg_create(const ppcg_operator* op, int64_t n, int32_t k, int32_t s
   if (opt) c->opt = *opt;
   if (c->opt.maxiter == 0) c->opt.maxiter = 500;
   c->delta = c->opt.sigma_floor > 0.0 ? c->opt.sigma_floor : 0.1 / (op->h * op->h);
-  c->n = n;
-  c->k = k;
-  c->nbuf = c->opt.nbuf;
-  c->kt = k + c->nbuf;
-  c->q = sbsize;
+  c->cplx = op->dtype == PPCG_C128;
+  const int f = c->cplx ? 2 : 1;
+  c->ng = n;
+  c->kc = k;
+  c->n = f * n;
+  c->k = f * k;
+  c->nbuf = f * c->opt.nbuf;
+  c->kt = c->k + c->nbuf;
+  c->q = f * sbsize;
+  c->grid.cplx = c->cplx ? 1 : 0;
+  for (int d = 0; d < 3; ++d) {
+    c->grid.ct[d] = std::cos(op->theta[d]);
+    c->grid.st[d] = std::sin(op->theta[d]);
+  }
   c->rr_period = rr_period;
   c->stream = (cudaStream_t)cuda_stream;
-  const Sizes sz = make_sizes(n, c->kt, sbsize);
+  const Sizes sz = make_sizes(c->n, c->kt, c->q);
   const Offsets o = layout(sz);
   c->ld = sz.ld;
   c->gpart_cap = sz.gpart_cap;
@@ -650,8 +667,10 @@ ppcg_status ppcg_create(const ppcg_operator* op, int64_t n, int32_t k, int32_t s
 
 ppcg_status ppcg_set_potential(ppcg_handle c, const double* V) {
   if (!c || !V) return PPCG_ERR_ARG;
-  CK(cudaMemcpyAsync(c->V, V, sizeof(double) * c->n, cudaMemcpyDefault, c->stream));
-  CK(make_diag(c->V, c->grid.inv_h2, c->n, c->dg, c->stream));
+  CK(cudaMemcpyAsync(c->V, V, sizeof(double) * c->ng, cudaMemcpyDefault, c->stream));
+  CK(make_diag(c->V, c->grid.inv_h2, c->ng, c->dg, c->stream));
+  if (c->cplx)   // the real form's diagonal is diag(A) twice
+    CK(cudaMemcpyAsync(c->dg + c->ng, c->dg, sizeof(double) * c->ng, cudaMemcpyDeviceToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return PPCG_OK;
 }
@@ -678,8 +697,14 @@ ppcg_status ppcg_solve(ppcg_handle c, const double* X0, double tol, double* lamb
   cudaStream_t s = c->stream;
   // pointers may be host or device (cudaMemcpyDefault resolves through unified addressing)
   phase_mark(c, PPCG_T_OTHER);
-  CK(cudaMemcpy2DAsync(c->X, ld * sizeof(double), X0, n * sizeof(double), n * sizeof(double), kt, cudaMemcpyDefault,
-                       s));
+  if (c->cplx) {
+    // complex X0 (ng x kt/2, interleaved) -> staging -> real form with J-paired columns
+    CK(cudaMemcpyAsync(c->Xs, X0, sizeof(double) * 2 * (size_t)c->ng * (kt / 2), cudaMemcpyDefault, s));
+    CK(cplx_to_realform(c->Xs, c->ng, c->ng, kt / 2, c->X, ld, s));
+  } else {
+    CK(cudaMemcpy2DAsync(c->X, ld * sizeof(double), X0, n * sizeof(double), n * sizeof(double), kt,
+                         cudaMemcpyDefault, s));
+  }
   CK(cudaMemsetAsync(c->icnt, 0, 4 * sizeof(int), s));
   SolveState st;
   st.k_lock = 0;
@@ -771,16 +796,26 @@ ppcg_status ppcg_solve(ppcg_handle c, const double* X0, double tol, double* lamb
   CK(reduce_colnorms(c->normpart, norm_row_tiles(n), k, c->norms, s));
   CK(cudaMemcpyAsync(c->nrm_h.data(), c->norms, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(c->lam_h.data(), c->lam, sizeof(double) * kt, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpy2DAsync(X, n * sizeof(double), c->Xs, ld * sizeof(double), n * sizeof(double), k, cudaMemcpyDefault,
-                       s));
+  if (c->cplx) {
+    // complex pair j is real-form column 2j (its partner 2j+1 is the same vector times i)
+    CK(realform_to_cplx(c->Xs, ld, c->ng, c->kc, c->W, c->ng, s));
+    CK(cudaMemcpyAsync(X, c->W, sizeof(double) * 2 * (size_t)c->ng * c->kc, cudaMemcpyDefault, s));
+  } else {
+    CK(cudaMemcpy2DAsync(X, n * sizeof(double), c->Xs, ld * sizeof(double), n * sizeof(double), k,
+                         cudaMemcpyDefault, s));
+  }
   CK(cudaMemcpyAsync(c->counters_h, c->icnt, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   phase_mark(c, PPCG_T_OTHER);
   phase_flush(c);
   double mx = 0.0;
-  for (int i = 0; i < k; ++i) {
-    lambda[i] = c->lam_h[i];
-    const double r = std::sqrt(c->nrm_h[i]);
+  const int f = c->cplx ? 2 : 1;
+  for (int i = 0; i < k / f; ++i) {
+    const double li = c->lam_h[f * i];
+    if (c->cplx && !(std::fabs(c->lam_h[f * i + 1] - li) <= 1e-6 * std::max(1.0, std::fabs(li))))
+      return PPCG_ERR_NUMERIC;   // the real form's eigenvalues must come in equal pairs
+    lambda[i] = li;
+    const double r = std::sqrt(c->nrm_h[f * i]);
     if (resnorm) resnorm[i] = r;
     if (!std::isfinite(r)) return PPCG_ERR_NUMERIC;
     mx = std::max(mx, r);
@@ -867,8 +902,9 @@ ppcg_status ppcg_residual(ppcg_handle c, const double* X, const double* HX, int6
 
 ppcg_status ppcg_energy_gradient(ppcg_handle c, const double* X, int64_t ld, int32_t k, double scale,
                                  double* grad_V) {
-  if (!c || !X || !grad_V || k < 1 || ld < c->n || !std::isfinite(scale)) return PPCG_ERR_ARG;
-  CK(density(X, ld, c->n, k, scale, grad_V, c->stream));
+  if (!c || !X || !grad_V || k < 1 || ld < c->ng || !std::isfinite(scale)) return PPCG_ERR_ARG;
+  if (c->cplx) CK(density_c(X, ld, c->ng, k, scale, grad_V, c->stream));
+  else CK(density(X, ld, c->n, k, scale, grad_V, c->stream));
   return PPCG_OK;
 }
 

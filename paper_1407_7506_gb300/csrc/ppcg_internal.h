@@ -32,6 +32,8 @@ long long launch_count();
 struct Grid {
   int nx, ny, nz;
   double inv_h2;
+  int cplx;          // 1: complex Bloch operator applied in the real form [u; v] (columns of 2 nx ny nz)
+  double ct[3], st[3];   // cos and sin of the Bloch twist per axis
 };
 
 // Y[:, c] = A X[:, c] for c < m; dg = 6/h^2 + V (n doubles).
@@ -107,6 +109,11 @@ cudaError_t density(const double* X, int64_t ld, int64_t n, int k, double scale,
 cudaError_t make_diag(const double* V, double inv_h2, int64_t n, double* dg, cudaStream_t s);
 // count non-finite entries of v[0..m) into *bad (device int)
 cudaError_t check_finite(const double* v, int m, int* bad, cudaStream_t s);
+// Complex (Bloch) problems in the real form: start block conversion, output extraction with the phase convention,
+// and the density sum_c |z_c|^2 of a complex block (interleaved re/im, leading dimensions in complex entries).
+cudaError_t cplx_to_realform(const double* Z, int64_t ldz, int64_t n, int kt, double* X, int64_t ldx, cudaStream_t s);
+cudaError_t realform_to_cplx(const double* Y, int64_t ldy, int64_t n, int k, double* Z, int64_t ldz, cudaStream_t s);
+cudaError_t density_c(const double* Z, int64_t ldz, int64_t n, int k, double scale, double* rho, cudaStream_t s);
 // Polar orthonormalisation helpers (m x m, leading dimension m): Y = G - I in place with fro2[0] = ||Y||_F^2;
 // Z = a Y + b I; Z += b I.
 cudaError_t eye_residual(double* G, int m, double* fro2, cudaStream_t s);

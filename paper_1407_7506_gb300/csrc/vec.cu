@@ -140,6 +140,88 @@ density_kernel(const double* __restrict__ X, int64_t ld, int64_t n, int k, doubl
   }
 }
 
+// ---- complex Hermitian (Bloch) problems, solved in the real form R = [[Re H, -Im H], [Im H, Re H]] of order 2n:
+// a complex vector z = u + i v is the real column [u; v]; J [u; v] = [-v; u] represents i z.
+
+// Complex start block Z (n x kt, interleaved re/im, leading dimension ldz complex entries) -> real form X
+// (2n x 2kt): column 2j = [Re z_j; Im z_j], column 2j+1 = J of it, so every pair spans a J-invariant plane.
+__global__ void cplx_to_realform_kernel(const double* __restrict__ Z, int64_t ldz, int64_t n, double* __restrict__ X,
+                                        int64_t ldx) {
+  const int j = blockIdx.y;
+  const double* z = Z + 2 * (int64_t)j * ldz;
+  double* a = X + (int64_t)(2 * j) * ldx;
+  double* b = a + ldx;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const double re = z[2 * p], im = z[2 * p + 1];
+    a[p] = re;
+    a[p + n] = im;
+    b[p] = -im;
+    b[p + n] = re;
+  }
+}
+
+// Output column j of a complex handle: z = Y[0:n, 2j] + i Y[n:2n, 2j], scaled to unit norm with its entry of
+// largest modulus (lowest index on ties) real positive; one block per column.
+__global__ void __launch_bounds__(1024)
+realform_to_cplx_kernel(const double* __restrict__ Y, int64_t ldy, int64_t n, double* __restrict__ Z, int64_t ldz) {
+  const double* u = Y + (int64_t)(2 * blockIdx.x) * ldy;
+  const double* v = u + n;
+  double* z = Z + 2 * (int64_t)blockIdx.x * ldz;
+  double sq = 0.0, best = -1.0;
+  int64_t bi = 0;
+  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+    const double a2 = u[r] * u[r] + v[r] * v[r];
+    sq += a2;
+    if (a2 > best) { best = a2; bi = r; }
+  }
+  __shared__ double s_sq[32], s_best[32];
+  __shared__ long long s_bi[32];
+  for (int off = 16; off > 0; off >>= 1) {
+    sq += __shfl_down_sync(0xffffffffu, sq, off);
+    const double ob = __shfl_down_sync(0xffffffffu, best, off);
+    const long long oi = __shfl_down_sync(0xffffffffu, (long long)bi, off);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  if (lane == 0) { s_sq[warp] = sq; s_best[warp] = best; s_bi[warp] = bi; }
+  __syncthreads();
+  __shared__ double sc_re, sc_im;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) / 32;
+    double t = 0.0, b = -1.0;
+    long long i = 0;
+    for (int w = 0; w < nw; ++w) {
+      t += s_sq[w];
+      if (s_best[w] > b || (s_best[w] == b && s_bi[w] < i)) { b = s_best[w]; i = s_bi[w]; }
+    }
+    const double mod = sqrt(u[i] * u[i] + v[i] * v[i]);
+    const double inv = (mod > 0.0 ? 1.0 / mod : 0.0) / sqrt(t);   // conj(z_p) / |z_p| / ||z||
+    sc_re = u[i] * inv;
+    sc_im = -v[i] * inv;
+  }
+  __syncthreads();
+  const double cr = sc_re, ci = sc_im;
+  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+    const double a = u[r], b = v[r];
+    z[2 * r] = a * cr - b * ci;
+    z[2 * r + 1] = a * ci + b * cr;
+  }
+}
+
+// rho[p] = scale * sum_{c < k} |Z[p, c]|^2 for a complex block (interleaved, leading dimension ldz complex)
+__global__ void __launch_bounds__(256)
+density_c_kernel(const double* __restrict__ Z, int64_t ldz, int64_t n, int k, double scale, double* __restrict__ rho) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int c = 0; c < k; ++c) {
+      const double2 z = __ldg(reinterpret_cast<const double2*>(Z + 2 * (p + (int64_t)c * ldz)));
+      s0 = fma(z.x, z.x, s0);
+      s1 = fma(z.y, z.y, s1);
+    }
+    rho[p] = scale * (s0 + s1);
+  }
+}
+
 __global__ void make_diag_kernel(const double* __restrict__ V, double six_inv_h2, int64_t n, double* dg) {
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
     dg[r] = six_inv_h2 + V[r];
@@ -253,6 +335,31 @@ cudaError_t density(const double* X, int64_t ld, int64_t n, int k, double scale,
   int64_t blocks = ceil_div(n, 256);
   if (blocks > 8192) blocks = 8192;
   density_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, ld, n, k, scale, rho);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t cplx_to_realform(const double* Z, int64_t ldz, int64_t n, int kt, double* X, int64_t ldx,
+                             cudaStream_t s) {
+  if (kt <= 0) return cudaSuccess;
+  const int64_t bx = ceil_div(n, 256);
+  cplx_to_realform_kernel<<<dim3((unsigned)(bx < 1024 ? bx : 1024), (unsigned)kt), 256, 0, s>>>(Z, ldz, n, X, ldx);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t realform_to_cplx(const double* Y, int64_t ldy, int64_t n, int k, double* Z, int64_t ldz,
+                             cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  realform_to_cplx_kernel<<<(unsigned)k, 1024, 0, s>>>(Y, ldy, n, Z, ldz);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t density_c(const double* Z, int64_t ldz, int64_t n, int k, double scale, double* rho, cudaStream_t s) {
+  int64_t blocks = ceil_div(n, 256);
+  if (blocks > 8192) blocks = 8192;
+  density_c_kernel<<<(unsigned)blocks, 256, 0, s>>>(Z, ldz, n, k, scale, rho);
   count_launch();
   return cudaGetLastError();
 }

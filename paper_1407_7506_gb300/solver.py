@@ -20,13 +20,14 @@ def _ptr(t):
 class Solver:
     """k smallest eigenpairs of A = -Laplacian_h + diag(V) on an N^3 (or nx x ny x nz) periodic grid.
 
+    dtype "c128" with a Bloch twist theta gives the complex Hermitian operator (start blocks and vectors complex).
     V: torch tensor (any device) or numpy array of n doubles. The workspace is a torch uint8 CUDA tensor owned
     by this object; the stream is torch's current stream unless one is given.
     """
 
     def __init__(self, V, grid, k, sbsize, rr_period=5, h=1.0, nbuf=0, maxiter=0, lock=True, timing=False,
                  sigma_floor=0.0, device="cuda", stream=None, history=0, precision="fp64", fp64_gemm="fma",
-                 orth="cholqr2", orth_skip_tol=0.0):
+                 orth="cholqr2", orth_skip_tol=0.0, dtype="f64", theta=(0.0, 0.0, 0.0)):
         if not torch.cuda.is_available():
             raise RuntimeError("the PPCG library needs a CUDA GPU; no CPU fallback exists")
         nx, ny, nz = (grid, grid, grid) if np.isscalar(grid) else tuple(grid)
@@ -36,7 +37,9 @@ class Solver:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self._V = torch.as_tensor(np.asarray(V) if not torch.is_tensor(V) else V, dtype=torch.float64)
         self._V = self._V.to(self.device).contiguous()
-        self.op = ppcg_operator(nx, ny, nz, h, self._V.data_ptr(), (ctypes.c_double * 3)(0.0, 0.0, 0.0), 0)
+        self.cplx = {"f64": False, "c128": True}[dtype]
+        self.dtype = torch.complex128 if self.cplx else torch.float64
+        self.op = ppcg_operator(nx, ny, nz, h, self._V.data_ptr(), (ctypes.c_double * 3)(*theta), 1 if self.cplx else 0)
         self.opt = ppcg_options()
         self.opt.maxiter = maxiter
         self.opt.nbuf = nbuf
@@ -68,8 +71,8 @@ class Solver:
             X0t = torch.from_numpy(np.ascontiguousarray(X0.T)).to(self.device)
         else:
             X0t = X0
-        assert X0t.shape == (self.k + self.nbuf, self.n) and X0t.dtype == torch.float64 and X0t.is_contiguous()
-        X = out if out is not None else torch.empty((self.k, self.n), dtype=torch.float64, device=self.device)
+        assert X0t.shape == (self.k + self.nbuf, self.n) and X0t.dtype == self.dtype and X0t.is_contiguous()
+        X = out if out is not None else torch.empty((self.k, self.n), dtype=self.dtype, device=self.device)
         lam = np.zeros(self.k)
         res = np.zeros(self.k)
         st = ppcg_stats()
@@ -123,8 +126,8 @@ class BatchSolver:
                     X0t = torch.from_numpy(np.ascontiguousarray(X0.T)).to(self.device)
                 else:
                     X0t = X0
-                X = torch.empty((s.k, s.n), dtype=torch.float64, device=self.device)
-            assert X0t.shape == (s.k + s.nbuf, s.n) and X0t.dtype == torch.float64 and X0t.is_contiguous()
+                X = torch.empty((s.k, s.n), dtype=s.dtype, device=self.device)
+            assert X0t.shape == (s.k + s.nbuf, s.n) and X0t.dtype == s.dtype and X0t.is_contiguous()
             lam, res, st = np.zeros(s.k), np.zeros(s.k), ppcg_stats()
             items[i].h = s.handle
             items[i].X0 = X0t.data_ptr()

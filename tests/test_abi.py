@@ -105,8 +105,11 @@ def test_invalid_option_values(lib, field, value):
 
 def test_unsupported_options_are_reported(lib):
     op = _op(16)
-    op.dtype = 1
+    op.dtype = 2                                        # no such dtype
     out = ctypes.c_size_t(0)
+    assert lib.ppcg_workspace_bytes(ctypes.byref(op), 4096, 8, 2, None, ctypes.byref(out)) == pk.PPCG_ERR_UNSUPPORTED
+    op = _op(16)
+    op.theta[1] = 0.5                                   # a Bloch twist needs the complex dtype
     assert lib.ppcg_workspace_bytes(ctypes.byref(op), 4096, 8, 2, None, ctypes.byref(out)) == pk.PPCG_ERR_UNSUPPORTED
     opt = pk.ppcg_options()
     opt.precision = 2                                   # BF16 mixed form: not provided
@@ -143,3 +146,17 @@ def test_batched_and_autotune_validate_arguments(lib):
     best = ctypes.c_int32(0)
     assert lib.ppcg_autotune_sbsize(None, 4096, 8, 5, None, None, 1e-8, None, 0, None, ctypes.byref(best),
                                     None) == pk.PPCG_ERR_ARG
+
+
+def test_complex_handles_size_the_real_form(lib):
+    # a C128 problem is solved in its real form of order 2n with 2(k + nbuf) columns and sub-blocks of 2 sbsize
+    real, cplx = _op(16), _op(16)
+    cplx.dtype = 1
+    cplx.theta[0] = 0.3
+    a, b = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    assert lib.ppcg_workspace_bytes(ctypes.byref(real), 4096, 8, 2, None, ctypes.byref(a)) == pk.PPCG_OK
+    assert lib.ppcg_workspace_bytes(ctypes.byref(cplx), 4096, 8, 2, None, ctypes.byref(b)) == pk.PPCG_OK
+    assert b.value > 2 * a.value
+    assert lib.ppcg_workspace_bytes(ctypes.byref(cplx), 4096, 16, 9, None, ctypes.byref(a)) == pk.PPCG_ERR_ARG
+    cplx.theta[2] = float("inf")
+    assert lib.ppcg_workspace_bytes(ctypes.byref(cplx), 4096, 8, 2, None, ctypes.byref(a)) == pk.PPCG_ERR_ARG

@@ -315,6 +315,40 @@ def test_ppcg_warm_start_converges_immediately():
     assert r.converged and r.iters == 0
 
 
+# ---------------------------------------------------------------- complex Hermitian (Bloch) problems
+THETA = (0.3, 0.7, 1.1)
+
+
+def test_ppcg_complex_bloch_matches_dense_eigh():
+    N, k = 6, 8
+    w = wl.small("cb", N=N, k=k, sbsize=2, potential="wells", n_wells=2, seed=3, dtype="c128", theta=THETA)
+    V, X0 = wl.make_inputs(w)
+    A = oracle.assemble_H(V, N, 1.0, THETA)
+    ev, U = np.linalg.eigh(A)
+    r = oracle.ppcg(V, N, 1.0, k, 2, 5, X0, tol=1e-8, theta=THETA, maxiter=3000)
+    assert r.converged and r.X.dtype == np.complex128
+    np.testing.assert_allclose(r.lam, ev[:k], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(r.X.conj().T @ r.X, np.eye(k), atol=1e-12)
+    res = np.linalg.norm(A @ r.X - r.X * r.lam[None, :], axis=0)
+    assert np.max(res) <= 1e-8 * (1 + 1e-6)
+    for i in range(k):                                # phase convention: largest-modulus entry real positive
+        p = int(np.argmax(np.abs(r.X[:, i])))
+        assert abs(r.X[p, i].imag) < 1e-14 and r.X[p, i].real > 0
+
+
+def test_ppcg_complex_zero_potential_closed_form_spectrum():
+    # V = 0: Bloch plane waves, eigenvalues sum_d 4 sin^2((2 pi m_d + theta_d) / (2 N)), all distinct for this twist
+    N, k = 5, 10
+    lam_all = np.sort([sum(4 * np.sin((2 * np.pi * m[d] + THETA[d]) / (2 * N)) ** 2 for d in range(3))
+                       for m in itertools.product(range(N), repeat=3)])
+    assert lam_all[k] - lam_all[k - 1] > 1e-3
+    w = wl.small("cz", N=N, k=k, sbsize=2, potential="zero", seed=4, dtype="c128", theta=THETA)
+    V, X0 = wl.make_inputs(w)
+    r = oracle.ppcg(V, N, 1.0, k, 2, 5, X0, tol=1e-9, theta=THETA, maxiter=3000)
+    assert r.converged
+    np.testing.assert_allclose(r.lam, lam_all[:k], rtol=0, atol=1e-12)
+
+
 # ---------------------------------------------------------------- orthonormalisation variants (Section 5.4, R10)
 def test_polar_series_sums_to_inverse_square_root():
     # the binomial series of (1 + y)^{-1/2}, summed far out, equals the closed form at scalar y
