@@ -115,7 +115,8 @@ def cpu_oracle_sample(w, iters):
     import oracle
     V, X0 = wl.make_inputs(w)
     t0 = time.perf_counter()
-    r = oracle.ppcg(V, w.N, w.h, w.k, w.sbsize, w.rr_period, X0, tol=w.tol, maxiter=iters)
+    r = oracle.ppcg(V, w.N, w.h, w.k, w.sbsize, w.rr_period, X0, tol=w.tol, maxiter=iters,
+                    theta=w.theta if w.dtype == "c128" else None)
     el = time.perf_counter() - t0
     return el, r
 
@@ -133,9 +134,9 @@ def oracle_full_iters():
     return None, lam
 
 
-def cpu_baseline(w, sample_iters, gpu_iters):
+def cpu_baseline(w, sample_iters, gpu_iters, stored=True):
     el, r = cpu_oracle_sample(w, sample_iters)
-    full_iters, _ = oracle_full_iters()
+    full_iters, _ = oracle_full_iters() if stored else (None, None)
     iters_target = full_iters or gpu_iters
     per_iter = el / max(1, r.iters)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
@@ -200,7 +201,9 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2", help="configuration index (1 = 16^3 k=64, 2 = 32^3 k=256)")
+    ap.add_argument("--workload", default="2",
+                    help="1 = 16^3 k=64, 2 = 32^3 k=256 (default), 4 = the 64-problem batch, "
+                         "5 = the complex Bloch recipe at 32^3 k=128")
     ap.add_argument("--maxiter", type=int, default=6000)
     ap.add_argument("--ref-iters", type=int, default=3, help="oracle iterations per reference-arm step")
     ap.add_argument("--cpu-iters", type=int, default=3, help="oracle iterations in the cpu_baseline sample")
@@ -218,7 +221,7 @@ def main():
                               "solves do not fit a bounded sample"}), flush=True)
             return 0
         return run_batched(args)
-    w = wl.CONFIGS[int(args.workload)]
+    w = wl.REDUCED[5] if args.workload == "5" else wl.CONFIGS[int(args.workload)]
     if args.impl == "reference":
         return run_reference(args, w)
 
@@ -241,12 +244,14 @@ def main():
     V, X0 = wl.make_inputs(w)
     V_d = torch.from_numpy(V).to(dev)
     X0_d = torch.from_numpy(np.ascontiguousarray(X0.T)).to(dev)         # (k, n) rows = columns of X0
-    _, gold = oracle_full_iters()
+    _, gold = oracle_full_iters() if args.workload == "2" else (None, None)
+    cplx = w.dtype == "c128"
+    sk = {"dtype": w.dtype, "theta": w.theta} if cplx else {}          # Solver arguments of the operator
 
     def run_form(precision, clk_sampler, fp64_gemm="fma", orth="cholqr2"):
         solver = pk.Solver(V_d, w.N, w.k, w.sbsize, rr_period=w.rr_period, maxiter=args.maxiter, device=dev,
-                           stream=stream, precision=precision, fp64_gemm=fp64_gemm, orth=orth)
-        X_out = torch.empty((w.k, w.n), dtype=torch.float64, device=dev)
+                           stream=stream, precision=precision, fp64_gemm=fp64_gemm, orth=orth, **sk)
+        X_out = torch.empty((w.k, w.n), dtype=solver.dtype, device=dev)
         for _ in range(args.warmup):
             solver.solve(X0_d, w.tol, out=X_out)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -278,7 +283,7 @@ def main():
         solver.close()
         # one more solve with per-phase timers (the paper's profile categories), outside the timed region
         ps = pk.Solver(V_d, w.N, w.k, w.sbsize, rr_period=w.rr_period, maxiter=args.maxiter, device=dev,
-                       stream=stream, timing=True, precision=precision, fp64_gemm=fp64_gemm, orth=orth)
+                       stream=stream, timing=True, precision=precision, fp64_gemm=fp64_gemm, orth=orth, **sk)
         _, _, _, pst = ps.solve(X0_d, w.tol)
         ps.close()
         return {"ms_per_step": ms / args.steps, "iters": iters // args.steps, "iters_per_s": iters / (ms / 1e3),
@@ -301,19 +306,19 @@ def main():
     launches = fp64["launches"]
     parity = fp64["parity"]
     phases = fp64["phase_ms"]
-    probe = pk.Solver(V_d, w.N, w.k, w.sbsize, rr_period=w.rr_period, maxiter=1, device=dev, stream=stream)
+    probe = pk.Solver(V_d, w.N, w.k, w.sbsize, rr_period=w.rr_period, maxiter=1, device=dev, stream=stream, **sk)
     roof = roofline(pk, probe, w, dev, stream)
     probe.close()
     roof_mixed = None
     if any(FORMS[f][0] == "mixed_tf32" for f in results):
         probe = pk.Solver(V_d, w.N, w.k, w.sbsize, rr_period=w.rr_period, maxiter=1, device=dev, stream=stream,
-                          precision="mixed_tf32")
+                          precision="mixed_tf32", **sk)
         roof_mixed = roofline_tc(pk, probe, w, dev, stream)
         probe.close()
     e2e = None if args.no_e2e else run_e2e(pk, w, V, X0, max(1, args.steps // 2), stream)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, args.cpu_iters, iters // max(1, args.steps))
+        cpu = cpu_baseline(w, args.cpu_iters, iters // max(1, args.steps), stored=args.workload == "2")
     if rank != 0:
         return 0
     line = {
@@ -321,7 +326,11 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "n": w.n, "k": w.k, "sbsize": w.sbsize, "rr_period": w.rr_period,
-                   "tol": w.tol, "form": first, "potential": f"{w.n_wells} Gaussian wells + U[0,0.1) noise",
+                   "tol": w.tol, "form": first,
+                   "potential": (f"{w.n_wells} Gaussian wells + U[0,0.1) noise" if w.potential == "wells"
+                                 else "V ~ U[0,1)"),
+                   "operator": (f"complex Bloch twist {w.theta}, solved in the real form of order 2n"
+                                if w.dtype == "c128" else "real symmetric"),
                    "l2": f"no flush: working set {7 * w.n * w.k * 8 / 2**20:.0f} MiB > {L2_BYTES // 2**20} MiB L2"},
         "iters": fp64["iters"], "iters_per_s": fp64["iters_per_s"], "wall_s_per_step": fp64["wall_s_per_step"],
         "parity": parity, "roofline": roof, "phase_ms": phases, "jacobi_sweeps_max": fp64["jacobi_sweeps_max"],
@@ -446,7 +455,8 @@ def run_batched(args):
 
 def roofline(pk, solver, w, dev, stream):
     import torch
-    n, k = w.n, w.k
+    f = 2 if w.dtype == "c128" else 1            # a complex handle's GEMMs run on the real form: 2n x 2k
+    n, k = f * w.n, f * w.k
     g = torch.Generator(device="cpu").manual_seed(1)
     A = torch.randn((k, n), generator=g, dtype=torch.float64).to(dev)
     B = torch.randn((k, n), generator=g, dtype=torch.float64).to(dev)
@@ -482,7 +492,8 @@ def hbm_peak():
 def roofline_tc(pk, solver, w, dev, stream):
     """Mixed form: the tcgen05 TF32 Gram X^T W reads FP64 inputs; HBM is its bound at k = 256."""
     import torch
-    n, k = w.n, w.k
+    f = 2 if w.dtype == "c128" else 1
+    n, k = f * w.n, f * w.k
     g = torch.Generator(device="cpu").manual_seed(2)
     A = torch.randn((k, n), generator=g, dtype=torch.float64).to(dev)
     B = torch.randn((k, n), generator=g, dtype=torch.float64).to(dev)
@@ -511,12 +522,13 @@ def run_e2e(pk, w, V, X0, steps, stream):
     """The same solve through the C ABI with host buffers: copies in/out are inside the timed region."""
     import torch
     n, k = w.n, w.k
+    cplx = w.dtype == "c128"
     Vh = torch.from_numpy(V).pin_memory()
     X0h = torch.from_numpy(np.ascontiguousarray(X0.T)).pin_memory()
-    Xh = torch.empty((k, n), dtype=torch.float64).pin_memory()
+    Xh = torch.empty((k, n), dtype=torch.complex128 if cplx else torch.float64).pin_memory()
     lam = np.zeros(k)
     res = np.zeros(k)
-    op = pk.ppcg_operator(w.N, w.N, w.N, w.h, Vh.data_ptr(), (ctypes.c_double * 3)(0, 0, 0), 0)
+    op = pk.ppcg_operator(w.N, w.N, w.N, w.h, Vh.data_ptr(), (ctypes.c_double * 3)(*w.theta), 1 if cplx else 0)
     opt = pk.ppcg_options()
     opt.maxiter = 6000
     h = pk.ppcg_create(op, n, k, w.sbsize, w.rr_period, opt, stream.cuda_stream)
@@ -530,7 +542,8 @@ def run_e2e(pk, w, V, X0, steps, stream):
         el = (time.perf_counter() - t0) / steps
     finally:
         pk.ppcg_destroy(h)
-    return {"value": el, "unit": "s", "h2d_bytes_per_step": 8 * n + 8 * n * k, "d2h_bytes_per_step": 8 * n * k + 16 * k,
+    es = 16 if cplx else 8
+    return {"value": el, "unit": "s", "h2d_bytes_per_step": 8 * n + es * n * k, "d2h_bytes_per_step": es * n * k + 16 * k,
             "steps": steps, "max_residual": float(np.max(res))}
 
 

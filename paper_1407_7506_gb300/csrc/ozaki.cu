@@ -53,8 +53,13 @@ __device__ __forceinline__ uint32_t tile_off(int row, int k) {
   return (uint32_t)(row >> 3) * kSBO + (uint32_t)(row & 7) * 16u + (uint32_t)(k >> 3) * kLBO + (uint32_t)(k & 7) * 2u;
 }
 
-// 8 balanced base-128 digits of round(x 2^(54 - E)), most significant first; integer operations only
-__device__ __forceinline__ void digits(double x, int E, int (&d)[kDig]) {
+// Balanced base-128 digits of T = round(x 2^(54 - E)) (|T| <= 2^54), through one biased integer: adding
+// kBias = 63 (1 + 128 + ... + 128^7) makes T' = T + kBias lie in (0, 2^56), and the eight plain 7-bit fields u_f of
+// T' give the balanced digits u_f - 63 in [-63, 64] (the representation is unique, so these are the digits of T).
+// Digit j (j = 0 most significant) is field 7 - j. A field becomes an exact float by the 2^23 bit-pattern trick.
+constexpr long long kBias = 35745105703854015LL;   // 63 * (2^56 - 1) / 127
+
+__device__ __forceinline__ unsigned long long biased_digits(double x, int E) {
   const long long bits = __double_as_longlong(x);
   const int ex = (int)((bits >> 52) & 0x7FF);
   long long T = 0;
@@ -65,17 +70,17 @@ __device__ __forceinline__ void digits(double x, int E, int (&d)[kDig]) {
     else if (sh > -63) T = (m + (1LL << (-sh - 1))) >> (-sh);
     if (bits < 0) T = -T;
   }
-#pragma unroll
-  for (int j = kDig - 1; j >= 0; --j) {
-    int r = (int)(T & 127);
-    r = r > 64 ? r - 128 : r;
-    d[j] = r;
-    T = (T - r) >> 7;
-  }
+  return (unsigned long long)(T + kBias);
 }
 
-__device__ __forceinline__ uint32_t pack_bf16x2(int lo, int hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn((float)lo, (float)hi);
+__device__ __forceinline__ float digit_of(unsigned long long t, int j) {
+  const uint32_t u = (uint32_t)(t >> (7 * (kDig - 1 - j))) & 127u;
+  return __uint_as_float(0x4B000000u | u) - 8388671.0f;          // (2^23 + u) - (2^23 + 63), exact
+}
+
+// digit j of two elements as a packed BF16 pair (exact: |digit| <= 64)
+__device__ __forceinline__ uint32_t digit_pair(unsigned long long t0, unsigned long long t1, int j) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(digit_of(t0, j), digit_of(t1, j));
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
@@ -244,13 +249,11 @@ oz_gram_kernel(const double* __restrict__ A, int64_t lda, const double* __restri
       const int cm = warp + i * (kThreads / 32);
       const int g8 = cm / (kBK / 8), c8 = cm % (kBK / 8);
       const int E = sm.Ea[8 * g8 + rr];
-      int d0[kDig], d1[kDig];
-      digits(reg.a[i][0], E, d0);
-      digits(reg.a[i][1], E, d1);
+      const unsigned long long t0 = biased_digits(reg.a[i][0], E), t1 = biased_digits(reg.a[i][1], E);
       const uint32_t off = tile_off(8 * g8 + rr, 8 * c8 + 2 * kp);
 #pragma unroll
       for (int j = 0; j < kDig; ++j)
-        *reinterpret_cast<uint32_t*>(stage + j * kAPlane + off) = pack_bf16x2(d0[j], d1[j]);
+        *reinterpret_cast<uint32_t*>(stage + j * kAPlane + off) = digit_pair(t0, t1, j);
     }
     uint8_t* bst = stage + kDig * kAPlane;
 #pragma unroll
@@ -258,13 +261,11 @@ oz_gram_kernel(const double* __restrict__ A, int64_t lda, const double* __restri
       const int cm = warp + i * (kThreads / 32);
       const int g8 = cm / (kBK / 8), c8 = cm % (kBK / 8);
       const int E = sm.Eb[8 * g8 + rr];
-      int d0[kDig], d1[kDig];
-      digits(reg.b[i][0], E, d0);
-      digits(reg.b[i][1], E, d1);
+      const unsigned long long t0 = biased_digits(reg.b[i][0], E), t1 = biased_digits(reg.b[i][1], E);
       const uint32_t off = tile_off(8 * g8 + rr, 8 * c8 + 2 * kp);
 #pragma unroll
       for (int j = 0; j < kDig; ++j)
-        *reinterpret_cast<uint32_t*>(bst + j * kBPlane + off) = pack_bf16x2(d0[j], d1[j]);
+        *reinterpret_cast<uint32_t*>(bst + j * kBPlane + off) = digit_pair(t0, t1, j);
     }
   };
   int gstage = 0;
@@ -369,13 +370,11 @@ oz_update_kernel(const double* __restrict__ A, int64_t lda, const double* __rest
       const int cm = warp + i * (kThreads / 32);
       const int g8 = cm / (kBK / 8), c8 = cm % (kBK / 8);
       const int E = sm.Ea[8 * g8 + rr];
-      int d0[kDig], d1[kDig];
-      digits(reg.a[i][0], E, d0);
-      digits(reg.a[i][1], E, d1);
+      const unsigned long long t0 = biased_digits(reg.a[i][0], E), t1 = biased_digits(reg.a[i][1], E);
       const uint32_t off = tile_off(8 * g8 + rr, 8 * c8 + 2 * kp);
 #pragma unroll
       for (int j = 0; j < kDig; ++j)
-        *reinterpret_cast<uint32_t*>(stage + j * kAPlane + off) = pack_bf16x2(d0[j], d1[j]);
+        *reinterpret_cast<uint32_t*>(stage + j * kAPlane + off) = digit_pair(t0, t1, j);
     }
     uint8_t* bst = stage + kDig * kAPlane;
 #pragma unroll
@@ -383,13 +382,11 @@ oz_update_kernel(const double* __restrict__ A, int64_t lda, const double* __rest
       const int cm = warp + i * (kThreads / 32);
       const int g8 = cm / (kBK / 8), c8 = cm % (kBK / 8);
       const int E = sm.Eb[8 * g8 + rr];
-      int d0[kDig], d1[kDig];
-      digits(reg.b[i][0], E, d0);
-      digits(reg.b[i][1], E, d1);
+      const unsigned long long t0 = biased_digits(reg.b[i][0], E), t1 = biased_digits(reg.b[i][1], E);
       const uint32_t off = tile_off(8 * g8 + rr, 8 * c8 + 2 * kp);
 #pragma unroll
       for (int j = 0; j < kDig; ++j)
-        *reinterpret_cast<uint32_t*>(bst + j * kBPlane + off) = pack_bf16x2(d0[j], d1[j]);
+        *reinterpret_cast<uint32_t*>(bst + j * kBPlane + off) = digit_pair(t0, t1, j);
     }
   };
   int gstage = 0;

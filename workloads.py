@@ -60,6 +60,14 @@ CONFIGS = {
 }
 
 
+# Configurations too large to converge within a benchmark run on one GPU, at the largest size that does: the
+# config-5 recipe (Bloch twist, Gaussian wells + noise, complex vectors) on a 32^3 grid with k = 128.
+REDUCED = {
+    5: Workload("grid32_k128_q4_wells8_bloch", N=32, k=128, sbsize=4, potential="wells", n_wells=8, seed=1005,
+                dtype="c128", theta=(0.3, 0.7, 1.1)),
+}
+
+
 def batch(count: int = 64, seed: int = 1004, n_range=(12, 28), k_range=(32, 256), sbsize: int = 4):
     """The batched workload: `count` independent uniform-potential problems of uneven size (config 4 with the
     defaults). Returns a list of Workloads; make_inputs(w) draws each problem's V and X0 from its own seed."""
