@@ -58,6 +58,8 @@ struct ppcg_ctx {
   bool mixed = false;      // PPCG_MIXED_TF32: projections and the first CholQR Gram on tcgen05
   bool ozaki = false;      // FP64 n x k GEMMs emulated on the BF16 tensor cores (error-free splitting)
   int* ozexps = nullptr;   // exponent workspace of the emulated GEMMs
+  uint8_t* ozimg = nullptr;   // digit images of the emulated Grams' operands
+  size_t ozimg_bytes = 0;
   int* tcflag = nullptr;   // timeout flag of the tensor-core kernels
   bool cplx = false;       // complex Hermitian (Bloch) problem, solved in the real form of order 2 ng
   int64_t ng = 0;          // grid points (the complex order); n = 2 ng for a complex handle
@@ -81,9 +83,10 @@ struct Sizes {
   int64_t n, ld;
   int kt, q, smax;
   size_t gpart_cap, bpart_cap;
+  size_t ozimg_bytes;   // digit images of the Ozaki Grams (0 unless the FP64 GEMMs are emulated)
 };
 
-Sizes make_sizes(int64_t n, int kt, int q) {
+Sizes make_sizes(int64_t n, int kt, int q, bool ozaki) {
   Sizes s{};
   s.n = n;
   s.ld = ceil_div(n, 32) * 32;
@@ -97,13 +100,14 @@ Sizes make_sizes(int64_t n, int kt, int q) {
   if (cap < kk) cap = kk;
   s.gpart_cap = cap;
   s.bpart_cap = block_gram_part_elems(n, kt, q);
+  s.ozimg_bytes = ozaki ? oz_img_bytes(n, kt) : 0;
   return s;
 }
 
 // Offsets of every region; returns the total byte count.
 struct Offsets {
   size_t V, dg, blk[7], G, M, C, Rinv, lam, norms, normpart, gpart, bpart, coef, cholws, jacws;
-  size_t iflag, icnt, jinfo, idx, bflags, bar, ozexps;
+  size_t iflag, icnt, jinfo, idx, bflags, bar, ozexps, ozimg;
   size_t total;
 };
 
@@ -134,6 +138,7 @@ Offsets layout(const Sizes& s) {
   o.bflags = L.off(s.smax, 4);
   o.bar = L.off(barrier_words(), 4);
   o.ozexps = L.off(oz_exp_elems(s.n, s.kt), 4);
+  o.ozimg = L.off(s.ozimg_bytes, 1);
   o.total = L.bytes + kAlign;
   return o;
 }
@@ -220,7 +225,8 @@ ppcg_status gram(ppcg_ctx* c, const double* A, int64_t lda, const double* B, int
                  double* Cm, int ldc) {
   const bool sym = (A == B && lda == ldb && ma == mb);
   if (c->ozaki)
-    CK(oz_gram(A, lda, B, ldb, c->n, ma, mb, Cm, ldc, sym, c->gpart, c->gpart_cap, c->ozexps, c->tcflag, c->stream));
+    CK(oz_gram(A, lda, B, ldb, c->n, ma, mb, Cm, ldc, sym, c->gpart, c->gpart_cap, c->ozexps, c->ozimg,
+               c->ozimg_bytes, c->tcflag, c->stream));
   else
     CK(ppcg::gram(A, lda, B, ldb, c->n, ma, mb, Cm, ldc, sym, c->gpart, c->gpart_cap, c->stream));
   return PPCG_OK;
@@ -230,7 +236,8 @@ ppcg_status gram(ppcg_ctx* c, const double* A, int64_t lda, const double* B, int
 ppcg_status update(ppcg_ctx* c, const double* A, int64_t lda, const double* G, int ldg, int m, int p, double* Y,
                    int64_t ldy, Epi mode, bool g_upper) {
   if (c->ozaki)
-    CK(oz_update(A, lda, G, ldg, c->n, m, p, Y, ldy, mode, c->ozexps, c->tcflag, c->stream));
+    CK(oz_update(A, lda, G, ldg, c->n, m, p, Y, ldy, mode, c->ozexps, c->ozimg, c->ozimg_bytes, c->tcflag,
+                 c->stream));
   else
     CK(gemm_nn(A, lda, G, ldg, c->n, m, p, Y, ldy, nullptr, 0, mode, g_upper, nullptr, c->stream));
   return PPCG_OK;
@@ -576,7 +583,7 @@ ppcg_status ppcg_workspace_bytes(const ppcg_operator* op, int64_t n, int32_t k, 
   PS(check_args(op, n, k, sbsize, 1, opt));
   const int kt = k + (opt ? opt->nbuf : 0);
   const int f = op->dtype == PPCG_C128 ? 2 : 1;
-  *bytes = layout(make_sizes(f * n, f * kt, f * sbsize)).total;
+  *bytes = layout(make_sizes(f * n, f * kt, f * sbsize, opt && opt->fp64_gemm == 1)).total;
   return PPCG_OK;
 }
 
@@ -615,7 +622,7 @@ ppcg_status ppcg_create(const ppcg_operator* op, int64_t n, int32_t k, int32_t s
   }
   c->rr_period = rr_period;
   c->stream = (cudaStream_t)cuda_stream;
-  const Sizes sz = make_sizes(c->n, c->kt, c->q);
+  const Sizes sz = make_sizes(c->n, c->kt, c->q, c->opt.fp64_gemm == 1);
   const Offsets o = layout(sz);
   c->ld = sz.ld;
   c->gpart_cap = sz.gpart_cap;
@@ -654,6 +661,8 @@ ppcg_status ppcg_create(const ppcg_operator* op, int64_t n, int32_t k, int32_t s
   c->mixed = (c->opt.precision == PPCG_MIXED_TF32);
   c->ozaki = (c->opt.fp64_gemm == 1);
   c->ozexps = reinterpret_cast<int*>(b + o.ozexps);
+  c->ozimg = sz.ozimg_bytes ? reinterpret_cast<uint8_t*>(b + o.ozimg) : nullptr;
+  c->ozimg_bytes = sz.ozimg_bytes;
   c->lam_h.assign(c->kt, 0.0);
   c->nrm_h.assign(c->kt, 0.0);
   ppcg_status st = ppcg_set_potential(c, op->V);

@@ -90,30 +90,68 @@ __device__ __forceinline__ double pow2(int e) {   // 2^e for e in the normal ran
 }
 
 // ------------------------------------------------------------------------------------------ exponent bounds
-// E[c] = smallest e with max_r |M[r, c]| < 2^e (kNoExp for a zero column); one warp per column
-__global__ void col_exp_kernel(const double* __restrict__ M, int64_t ld, int64_t rows, int cols, int* __restrict__ E) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x & 31;
-  if (warp >= cols) return;
-  const double* col = M + (int64_t)warp * ld;
+// E[c] = smallest e with max_r |M[r, c]| < 2^e (kNoExp for a zero line). Each block reduces a slice of lines and
+// merges its bound with atomicMax (the bound is monotone in the maximum), so a column of n rows is read by many
+// CTAs at once; E must hold kNoExp beforehand (fill_exp_kernel). NaN entries are ignored.
+__device__ __forceinline__ int exp_bound(double mx) {
+  const long long b = __double_as_longlong(mx);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  return (mx == 0.0 || ex == 0) ? kNoExp : ex - 1022;     // mx in [2^(ex-1023), 2^(ex-1022))
+}
+
+__global__ void fill_exp_kernel(int* E, int count) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) E[i] = kNoExp;
+}
+
+constexpr int kExpRows = 4096;    // rows per block of the column bound
+
+// grid (cols, ceil(rows / kExpRows)); 256 threads stride over the block's rows of column blockIdx.x
+__global__ void __launch_bounds__(256)
+col_exp_kernel(const double* __restrict__ M, int64_t ld, int64_t rows, int* __restrict__ E) {
+  const int col = blockIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.y * kExpRows;
+  const int64_t r1 = min(rows, r0 + kExpRows);
+  const double* c = M + (int64_t)col * ld;
   double mx = 0.0;
-  for (int64_t r = lane; r < rows; r += 32) mx = fmax(mx, fabs(__ldg(col + r)));
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) mx = fmax(mx, fabs(__ldg(c + r)));
   for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-  if (lane == 0) {
-    const long long b = __double_as_longlong(mx);
-    const int ex = (int)((b >> 52) & 0x7FF);
-    E[warp] = (mx == 0.0 || ex == 0) ? kNoExp : ex - 1022;   // mx in [2^(ex-1023), 2^(ex-1022))
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x / 32); ++w) mx = fmax(mx, red[w]);
+    const int e = exp_bound(mx);
+    if (e != kNoExp) atomicMax(E + col, e);
   }
 }
 
-// E[r] = smallest e with max_c |M[r, c]| < 2^e; one thread per row
+constexpr int kExpCols = 32;      // columns per block of the row bound
+
+// E[r] = smallest e with max_c |M[r, c]| < 2^e; grid (ceil(rows / 256), ceil(cols / kExpCols)), one thread per row
 __global__ void row_exp_kernel(const double* __restrict__ M, int64_t ld, int64_t rows, int cols, int* __restrict__ E) {
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
-    double mx = 0.0;
-    for (int c = 0; c < cols; ++c) mx = fmax(mx, fabs(__ldg(M + r + (int64_t)c * ld)));
-    const long long b = __double_as_longlong(mx);
-    const int ex = (int)((b >> 52) & 0x7FF);
-    E[r] = (mx == 0.0 || ex == 0) ? kNoExp : ex - 1022;
-  }
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  const int c0 = blockIdx.y * kExpCols;
+  const int c1 = min(cols, c0 + kExpCols);
+  double mx = 0.0;
+  for (int c = c0; c < c1; ++c) mx = fmax(mx, fabs(__ldg(M + r + (int64_t)c * ld)));
+  const int e = exp_bound(mx);
+  if (e != kNoExp) atomicMax(E + r, e);
+}
+
+cudaError_t col_exps(const double* M, int64_t ld, int64_t rows, int cols, int* E, cudaStream_t s) {
+  fill_exp_kernel<<<(unsigned)ceil_div(cols, 256), 256, 0, s>>>(E, cols);
+  col_exp_kernel<<<dim3((unsigned)cols, (unsigned)ceil_div(rows, kExpRows)), 256, 0, s>>>(M, ld, rows, E);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t row_exps(const double* M, int64_t ld, int64_t rows, int cols, int* E, cudaStream_t s) {
+  const int64_t b = ceil_div(rows, 256);
+  fill_exp_kernel<<<(unsigned)(b < 4096 ? b : 4096), 256, 0, s>>>(E, (int)rows);
+  row_exp_kernel<<<dim3((unsigned)b, (unsigned)ceil_div(cols, kExpCols)), 256, 0, s>>>(M, ld, rows, cols, E);
+  count_launch(2);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------------------------ shared machinery
@@ -447,6 +485,245 @@ oz_update_kernel(const double* __restrict__ A, int64_t lda, const double* __rest
   oz_teardown(sm, tmem, ok, gstage, flag);
 }
 
+// ------------------------------------------------------------------------------------------ pre-sliced Grams
+// The Gram's operands are sliced once, by a streaming kernel, into "digit images": for every TW-column tile t
+// (TW = 128 for the A role, 64 for the B role) and every 16-row block b of the operand, 8 planes (one per digit),
+// each the exact shared-memory image of a TW-row x 16-K operand tile in the canonical K-major layout (core
+// matrices of 8 rows x 16 bytes; 128 B between core matrices along K, 256 B between 8-row groups). The 8 planes of
+// a (t, b) pair are contiguous, so one bulk asynchronous copy (cp.async.bulk) per operand and stage moves them into
+// shared memory, through a 4-deep mbarrier pipeline: no digit arithmetic sits in the Gram's main loop and every
+// operand element is sliced once instead of once per output tile.
+constexpr int kSK = 16;                                   // K per stage
+constexpr uint32_t kSSBO = (kSK / 8) * 128;              // 256 B between 8-row groups
+constexpr uint32_t kSImg = (64 / 8) * kSSBO;             // 2 KB: one 64-row plane
+constexpr uint32_t kSAPlane = 2 * kSImg;                 // 128 rows
+constexpr uint32_t kSBPlane = kSImg;                     // 64 rows
+constexpr uint32_t kSStage = kDig * (kSAPlane + kSBPlane);   // 48 KB
+constexpr int kSBuf = 4;
+constexpr int kSChunkBlocks = kChunk / kSK;             // 16 stages per exact-accumulation chunk
+
+__device__ __forceinline__ uint32_t tile_off16(int row, int k) {
+  return (uint32_t)(row >> 3) * kSSBO + (uint32_t)(row & 7) * 16u + (uint32_t)(k >> 3) * 128u + (uint32_t)(k & 7) * 2u;
+}
+
+// One CTA per (TW-column tile, 16-row block): 16 TW elements, 8 digit planes of 32 TW bytes. Warp w stages core
+// matrices w, w + 8, ... (row group g8 = cm / 2, K group c8 = cm % 2); lane (rr, kp) holds rows 2 kp, 2 kp + 1 of
+// column rr of its core matrix.
+template <int TW>
+__global__ void __launch_bounds__(256)
+oz_slice_kernel(const double* __restrict__ M, int64_t ld, int64_t nrows, int ncols, const int* __restrict__ E,
+                uint8_t* __restrict__ img, int nkb) {
+  constexpr uint32_t plane = (TW / 8) * kSSBO;
+  const int tile = blockIdx.x / nkb, kb = blockIdx.x % nkb;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  const int rr = lane >> 2, kp = lane & 3;
+  uint8_t* out = img + ((size_t)tile * nkb + kb) * kDig * plane;
+#pragma unroll
+  for (int i = 0; i < TW / 32; ++i) {
+    const int cm = warp + 8 * i;
+    const int g8 = cm >> 1, c8 = cm & 1;
+    const int col = tile * TW + 8 * g8 + rr;
+    const int64_t r = (int64_t)kb * kSK + 8 * c8 + 2 * kp;
+    const bool cok = col < ncols;
+    const double* p = M + r + (int64_t)col * ld;
+    const double x0 = (cok && r < nrows) ? __ldg(p) : 0.0;
+    const double x1 = (cok && r + 1 < nrows) ? __ldg(p + 1) : 0.0;
+    const int Ec = cok ? __ldg(E + col) : kNoExp;
+    const unsigned long long t0 = biased_digits(x0, Ec), t1 = biased_digits(x1, Ec);
+    const uint32_t off = tile_off16(8 * g8 + rr, 8 * c8 + 2 * kp);
+#pragma unroll
+    for (int j = 0; j < kDig; ++j) *reinterpret_cast<uint32_t*>(out + j * plane + off) = digit_pair(t0, t1, j);
+  }
+}
+
+struct OzImgSmem {
+  uint64_t full[kSBuf];
+  uint64_t empty[kSBuf];
+  uint32_t tmem_slot;
+  int ok;
+  int Ea[kM];
+  int Eb[kN];
+};
+
+// Image-fed product. Gram (UPD = false): out = the split's FP64 partial of A^T B (ma x mb, leading dimension ma),
+// A/B the column images; Ea/Eb column exponents. Update (UPD = true): out = Y (ma = n rows, mb = p columns,
+// leading dimension ldo) receives A G (mode Store) or Y - A G (mode Sub), A the row image of the n x m operand
+// (row exponents Ea), B the column image of G (column exponents Eb). grid (tiles_m * tiles_n, nsplit); the split
+// covers 16-row (16-column for the update) blocks [y * kb_per_split, min(nkb, (y + 1) * kb_per_split)).
+struct ImgArgs {
+  const uint8_t* imgA;
+  const uint8_t* imgB;
+  int nkb, ma, mb, tiles_n, kb_per_split;
+  const int* Ea;
+  const int* Eb;
+  double* out;
+  int64_t ldo;
+  int symmetric, mode;
+  int* flag;
+};
+
+template <bool UPD>
+__global__ void __launch_bounds__(kThreads, 1) oz_img_kernel(ImgArgs a) {
+  extern __shared__ __align__(1024) uint8_t dyn[];
+  __shared__ OzImgSmem sm;
+  const int tm = blockIdx.x / a.tiles_n, tn = blockIdx.x % a.tiles_n;
+  const int m0 = tm * kM, n0 = tn * kN;
+  if (!UPD && a.symmetric && n0 + kN <= m0) return;   // entirely below the diagonal: the reduce reads only i <= j
+  const int kb0 = blockIdx.y * a.kb_per_split;
+  const int kb1 = min(a.nkb, kb0 + a.kb_per_split);
+  const int nst = kb1 > kb0 ? kb1 - kb0 : 0;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < kM; i += kThreads) sm.Ea[i] = (m0 + i < a.ma) ? a.Ea[m0 + i] : kNoExp;
+  for (int i = tid; i < kN; i += kThreads) sm.Eb[i] = (n0 + i < a.mb) ? a.Eb[n0 + i] : kNoExp;
+  if (tid == 0) {
+    for (int b = 0; b < kSBuf; ++b) {
+      mbar_init(smem_u32(&sm.full[b]), 1);
+      mbar_init(smem_u32(&sm.empty[b]), 1);
+    }
+    sm.ok = 1;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (tid / 32 == 0) tmem_alloc(smem_u32(&sm.tmem_slot), 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sm.tmem_slot;
+  const int warp = tid / 32, lane = tid & 31;
+  const int q = warp & 3, h = warp >> 2;
+  const uint8_t* srcA = a.imgA + (size_t)tm * a.nkb * kDig * kSAPlane;
+  const uint8_t* srcB = a.imgB + (size_t)tn * a.nkb * kDig * kSBPlane;
+  int issued = 0;                                 // stages whose copies were issued (thread 0)
+  auto issue = [&](int st) {                      // both operands of stage st into buffer st % kSBuf
+    const int b = st % kSBuf;
+    const uint32_t dst = smem_u32(dyn + b * kSStage);
+    const uint32_t fb = smem_u32(&sm.full[b]);
+    mbar_expect_tx(fb, kSStage);
+    bulk_g2s(dst, srcA + (size_t)(kb0 + st) * kDig * kSAPlane, kDig * kSAPlane, fb);
+    bulk_g2s(dst + kDig * kSAPlane, srcB + (size_t)(kb0 + st) * kDig * kSBPlane, kDig * kSBPlane, fb);
+    issued = st + 1;
+  };
+  float hi[32], lo[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) { hi[i] = 0.f; lo[i] = 0.f; }
+  if (tid == 0)
+    for (int st = 0; st < nst && st < kSBuf - 1; ++st) issue(st);
+  constexpr uint32_t idesc = idesc_bf16(kM, kN);
+  bool ok = true;
+  int consumed = 0;
+  for (int st = 0; st < nst; ++st) {
+    const int b = st % kSBuf;
+    const uint32_t use = (uint32_t)(st / kSBuf);
+    if (tid == 0 && sm.ok) {
+      if (!mbar_wait(smem_u32(&sm.full[b]), use & 1u)) {
+        sm.ok = 0;
+      } else {
+        consumed = st + 1;
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(dyn + b * kSStage), b0 = a0 + kDig * kSAPlane;
+        const bool first = (st % kSChunkBlocks) == 0;
+#pragma unroll
+        for (int g = 0; g < kGroups; ++g) {
+#pragma unroll
+          for (int j = 0; j <= g; ++j) {
+            mma_bf16(tmem + (uint32_t)(g * kN), smem_desc_nosw(a0 + j * kSAPlane, 128, kSSBO),
+                     smem_desc_nosw(b0 + (g - j) * kSBPlane, 128, kSSBO), idesc, (first && j == 0) ? 0u : 1u);
+          }
+        }
+        mma_commit(smem_u32(&sm.empty[b]));
+        const int next = st + kSBuf - 1;          // refill the buffer that stage st - 1 used
+        if (next < nst) {
+          if (next >= kSBuf) {
+            const int pb = next % kSBuf;
+            if (!mbar_wait(smem_u32(&sm.empty[pb]), (uint32_t)((next / kSBuf - 1) & 1))) sm.ok = 0;
+          }
+          if (sm.ok) issue(next);
+        }
+      }
+    }
+    const bool chunk_end = ((st + 1) % kSChunkBlocks) == 0 || st + 1 == nst;
+    if (chunk_end) {
+      if (tid == 0 && sm.ok && !mbar_wait(smem_u32(&sm.empty[b]), use & 1u)) sm.ok = 0;
+      __syncthreads();
+      if (!sm.ok) { ok = false; break; }
+      tc_fence_after();
+      fold_groups(tmem, q, h, hi, lo);
+      tc_fence_before();
+      __syncthreads();
+    }
+  }
+  if (ok) {
+    const int ri = 32 * q + lane;
+    const int gi = m0 + ri;
+    if (gi < a.ma) {
+      const int Ei = sm.Ea[ri];
+      double* row = UPD ? a.out + gi : a.out + (int64_t)blockIdx.y * a.ma * a.mb + gi;
+      const int64_t ld = UPD ? a.ldo : a.ma;
+      double yv[32];
+      if (UPD && a.mode != (int)Epi::Store) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int gj = n0 + 32 * h + i;
+          yv[i] = gj < a.mb ? row[(int64_t)gj * ld] : 0.0;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int cj = 32 * h + i;
+        const int gj = n0 + cj;
+        if (gj >= a.mb) continue;
+        const int Ej = sm.Eb[cj];
+        const double v = (nst == 0 || Ei == kNoExp || Ej == kNoExp) ? 0.0
+                                                                    : ((double)hi[i] + (double)lo[i]) * pow2(Ei + Ej - 10);
+        row[(int64_t)gj * ld] = (UPD && a.mode != (int)Epi::Store) ? yv[i] - v : v;
+      }
+    }
+  }
+  if (tid == 0 && !ok) {
+    atomicOr(a.flag, kFlagTimeout);
+    // wait (bounded) for the copies and MMAs still in flight before the CTA gives its memory back
+    for (int st = consumed; st < issued; ++st)
+      mbar_wait(smem_u32(&sm.full[st % kSBuf]), (uint32_t)((st / kSBuf) & 1));
+    if (consumed > 0)
+      mbar_wait(smem_u32(&sm.empty[(consumed - 1) % kSBuf]), (uint32_t)(((consumed - 1) / kSBuf) & 1));
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid / 32 == 0) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// Row image of an n x m operand for the update's A role: element (r, c) sits at M-row r, K index c; one CTA per
+// (128-row tile, 16-column block); row exponents Er.
+__global__ void __launch_bounds__(256)
+oz_slice_rows_kernel(const double* __restrict__ M, int64_t ld, int64_t nrows, int ncols, const int* __restrict__ Er,
+                     uint8_t* __restrict__ img, int nkb) {
+  const int tile = blockIdx.x / nkb, kb = blockIdx.x % nkb;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  const int rr = lane >> 2, kp = lane & 3;
+  uint8_t* out = img + ((size_t)tile * nkb + kb) * kDig * kSAPlane;
+#pragma unroll
+  for (int i = 0; i < kM / 32; ++i) {
+    const int cm = warp + 8 * i;
+    const int g8 = cm >> 1, c8 = cm & 1;
+    const int64_t r = (int64_t)tile * kM + 8 * g8 + rr;
+    const int c = kb * kSK + 8 * c8 + 2 * kp;
+    const bool rok = r < nrows;
+    const double x0 = (rok && c < ncols) ? __ldg(M + r + (int64_t)c * ld) : 0.0;
+    const double x1 = (rok && c + 1 < ncols) ? __ldg(M + r + (int64_t)(c + 1) * ld) : 0.0;
+    const int Ei = rok ? __ldg(Er + r) : kNoExp;
+    const unsigned long long t0 = biased_digits(x0, Ei), t1 = biased_digits(x1, Ei);
+    const uint32_t off = tile_off16(8 * g8 + rr, 8 * c8 + 2 * kp);
+#pragma unroll
+    for (int j = 0; j < kDig; ++j) *reinterpret_cast<uint32_t*>(out + j * kSAPlane + off) = digit_pair(t0, t1, j);
+  }
+}
+
+size_t oz_img_smem() { return (size_t)kSBuf * kSStage + 1024; }
+
 size_t oz_smem() { return 2 * (size_t)kStageBytes + 1024; }
 
 int sm_count() {
@@ -474,25 +751,70 @@ cudaError_t prep(const void* fn) {
 
 size_t oz_exp_elems(int64_t n, int cols) { return (size_t)(n > cols ? n : cols) + (size_t)cols + 64; }
 
+// one CTA per SM: the image kernels allocate all 512 TMEM columns
+cudaError_t prep_img(const void* fn) {
+  const size_t smem = oz_img_smem();
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  return per_sm <= 1 ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
+size_t oz_img_bytes(int64_t n, int cols) {   // one A-role (128-column tiles) plus one B-role (64-column) image
+  const size_t nkb = (size_t)ceil_div(n, kSK);
+  return ((size_t)ceil_div(cols, 128) * kSAPlane + (size_t)ceil_div(cols, 64) * kSBPlane) * nkb * kDig;
+}
+
 cudaError_t oz_gram(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n, int ma, int mb, double* C,
-                    int ldc, bool symmetric, double* part, size_t part_capacity, int* exps, int* flag,
-                    cudaStream_t s) {
+                    int ldc, bool symmetric, double* part, size_t part_capacity, int* exps, uint8_t* img,
+                    size_t img_bytes, int* flag, cudaStream_t s) {
   if (ma <= 0 || mb <= 0) return cudaSuccess;
   if ((size_t)ma * mb > part_capacity) return cudaErrorInvalidValue;
   int* Ea = exps;
   int* Eb = exps + ma;
-  col_exp_kernel<<<(unsigned)ceil_div(ma, 8), 256, 0, s>>>(A, lda, n, ma, Ea);
-  count_launch();
-  if (!(symmetric && A == B)) {
-    col_exp_kernel<<<(unsigned)ceil_div(mb, 8), 256, 0, s>>>(B, ldb, n, mb, Eb);
-    count_launch();
+  const bool same = symmetric && A == B;
+  cudaError_t e0 = col_exps(A, lda, n, ma, Ea, s);
+  if (e0 != cudaSuccess) return e0;
+  if (!same) {
+    e0 = col_exps(B, ldb, n, mb, Eb, s);
+    if (e0 != cudaSuccess) return e0;
   } else {
     Eb = Ea;
   }
-  cudaError_t e = prep((const void*)oz_gram_kernel);
-  if (e != cudaSuccess) return e;
   const int tiles_m = (int)ceil_div(ma, kM), tiles_n = (int)ceil_div(mb, kN);
   const int tiles = tiles_m * tiles_n;
+  const int64_t nkb64 = ceil_div(n, kSK);
+  const size_t bytesA = (size_t)ceil_div(ma, 128) * kSAPlane * kDig * nkb64;
+  const size_t bytesB = (size_t)ceil_div(mb, 64) * kSBPlane * kDig * nkb64;
+  if (img && img_bytes >= bytesA + bytesB && tiles_n >= 2) {
+    // several column tiles of B would each re-slice A: slice each operand once into digit images instead, then
+    // run the bulk-copy-fed Gram
+    const int nkb = (int)ceil_div(n, kSK);
+    uint8_t* imgA = img;
+    uint8_t* imgB = img + bytesA;
+    oz_slice_kernel<128><<<(unsigned)(ceil_div(ma, 128) * nkb), 256, 0, s>>>(A, lda, n, ma, Ea, imgA, nkb);
+    oz_slice_kernel<64><<<(unsigned)(ceil_div(mb, 64) * nkb), 256, 0, s>>>(B, ldb, n, mb, Eb, imgB, nkb);
+    count_launch(2);
+    const size_t smem = oz_img_smem();
+    cudaError_t e = prep_img((const void*)oz_img_kernel<false>);
+    if (e != cudaSuccess) return e;
+    int64_t nsplit = ceil_div(sm_count(), tiles);
+    const int64_t cap_rows = ceil_div(nkb, kSChunkBlocks);
+    const int64_t cap_mem = (int64_t)(part_capacity / ((size_t)ma * mb));
+    nsplit = std::max<int64_t>(1, std::min(nsplit, std::min(cap_rows, cap_mem)));
+    const int kps = (int)(ceil_div(ceil_div(nkb, nsplit), kSChunkBlocks) * kSChunkBlocks);
+    const int nsp = (int)ceil_div(nkb, kps);
+    const ImgArgs args{imgA, imgB, nkb, ma, mb, tiles_n, kps, Ea, Eb, part, ma, symmetric ? 1 : 0, 0, flag};
+    oz_img_kernel<false><<<dim3(tiles, nsp), kThreads, smem, s>>>(args);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return gram_reduce_partials(part, nsp, ma, mb, C, ldc, symmetric, s);
+  }
+  cudaError_t e = prep((const void*)oz_gram_kernel);
+  if (e != cudaSuccess) return e;
   int64_t nsplit = ceil_div(sm_count(), tiles);
   const int64_t cap_rows = ceil_div(n, kChunk);
   const int64_t cap_mem = (int64_t)(part_capacity / ((size_t)ma * mb));
@@ -508,16 +830,34 @@ cudaError_t oz_gram(const double* A, int64_t lda, const double* B, int64_t ldb, 
 }
 
 cudaError_t oz_update(const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p, double* Y,
-                      int64_t ldy, Epi mode, int* exps, int* flag, cudaStream_t s) {
+                      int64_t ldy, Epi mode, int* exps, uint8_t* img, size_t img_bytes, int* flag, cudaStream_t s) {
   if (p <= 0 || n <= 0) return cudaSuccess;
   int* Er = exps;
   int* Fc = exps + n;
-  int64_t blocks = ceil_div(n, 256);
-  row_exp_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(A, lda, n, m, Er);
-  count_launch();
-  col_exp_kernel<<<(unsigned)ceil_div(p, 8), 256, 0, s>>>(G, ldg, m, p, Fc);
-  count_launch();
-  cudaError_t e = prep((const void*)oz_update_kernel);
+  cudaError_t e = row_exps(A, lda, n, m, Er, s);
+  if (e != cudaSuccess) return e;
+  e = col_exps(G, ldg, m, p, Fc, s);
+  if (e != cudaSuccess) return e;
+  const int tiles_m = (int)ceil_div(n, kM), tiles_n = (int)ceil_div(p, kN);
+  const int nkb = (int)ceil_div(m, kSK);
+  const size_t bytesA = (size_t)tiles_m * nkb * kDig * kSAPlane;
+  const size_t bytesB = (size_t)tiles_n * nkb * kDig * kSBPlane;
+  if (img && img_bytes >= bytesA + bytesB && tiles_n >= 2) {
+    // several column tiles of G would each re-slice A: slice it once (row image) and feed the tensor cores by
+    // bulk copies
+    uint8_t* imgA = img;
+    uint8_t* imgB = img + bytesA;
+    oz_slice_rows_kernel<<<(unsigned)((int64_t)tiles_m * nkb), 256, 0, s>>>(A, lda, n, m, Er, imgA, nkb);
+    oz_slice_kernel<64><<<(unsigned)(tiles_n * nkb), 256, 0, s>>>(G, ldg, m, p, Fc, imgB, nkb);
+    count_launch(2);
+    e = prep_img((const void*)oz_img_kernel<true>);
+    if (e != cudaSuccess) return e;
+    const ImgArgs args{imgA, imgB, nkb, (int)n, p, tiles_n, nkb, Er, Fc, Y, ldy, 0, (int)mode, flag};
+    oz_img_kernel<true><<<dim3((unsigned)((int64_t)tiles_m * tiles_n), 1), kThreads, oz_img_smem(), s>>>(args);
+    count_launch();
+    return cudaGetLastError();
+  }
+  e = prep((const void*)oz_update_kernel);
   if (e != cudaSuccess) return e;
   oz_update_kernel<<<dim3((unsigned)ceil_div(n, kM), (unsigned)ceil_div(p, kN)), kThreads, oz_smem(), s>>>(
       A, lda, G, ldg, n, m, p, Y, ldy, (int)mode, Er, Fc, flag);

@@ -84,11 +84,14 @@ cudaError_t tc_update(const double* A, int64_t lda, const double* G, int ldg, in
 // FP64-accurate versions of gram / gemm_nn (Store or Sub) on the BF16 tensor cores by error-free splitting.
 // exps: int workspace of oz_exp_elems(n, max columns) entries.
 size_t oz_exp_elems(int64_t n, int cols);
+// img (img_bytes, may be NULL): workspace for the operands' digit images (oz_img_bytes(n, ma) + oz_img_bytes(n, mb));
+// with enough of it the Gram slices each operand once and feeds the tensor cores by bulk copies.
+size_t oz_img_bytes(int64_t n, int cols);
 cudaError_t oz_gram(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n, int ma, int mb, double* C,
-                    int ldc, bool symmetric, double* part, size_t part_capacity, int* exps, int* flag,
-                    cudaStream_t s);
+                    int ldc, bool symmetric, double* part, size_t part_capacity, int* exps, uint8_t* img,
+                    size_t img_bytes, int* flag, cudaStream_t s);
 cudaError_t oz_update(const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p, double* Y,
-                      int64_t ldy, Epi mode, int* exps, int* flag, cudaStream_t s);
+                      int64_t ldy, Epi mode, int* exps, uint8_t* img, size_t img_bytes, int* flag, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------------------- vectors
 // R = HX - X diag(lam); W = T R; norm_part per row tile.
