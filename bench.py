@@ -308,12 +308,19 @@ def main():
     phases = fp64["phase_ms"]
     probe = pk.Solver(V_d, w.N, w.k, w.sbsize, rr_period=w.rr_period, maxiter=1, device=dev, stream=stream, **sk)
     roof = roofline(pk, probe, w, dev, stream)
+    roof_stencil = roofline_stencil(pk, probe, w, dev, stream)
     probe.close()
     roof_mixed = None
     if any(FORMS[f][0] == "mixed_tf32" for f in results):
         probe = pk.Solver(V_d, w.N, w.k, w.sbsize, rr_period=w.rr_period, maxiter=1, device=dev, stream=stream,
                           precision="mixed_tf32", **sk)
         roof_mixed = roofline_tc(pk, probe, w, dev, stream)
+        probe.close()
+    roof_oz = None
+    if any(FORMS[f][1] == "ozaki" for f in results):
+        probe = pk.Solver(V_d, w.N, w.k, w.sbsize, rr_period=w.rr_period, maxiter=1, device=dev, stream=stream,
+                          fp64_gemm="ozaki", **sk)
+        roof_oz = roofline_ozaki(pk, probe, w, dev, stream)
         probe.close()
     e2e = None if args.no_e2e else run_e2e(pk, w, V, X0, max(1, args.steps // 2), stream)
     cpu = None
@@ -344,6 +351,8 @@ def main():
                    "counts": f["counts"]}
             for name, f in results.items()},
         "roofline_tf32_gram": roof_mixed,
+        "roofline_stencil": roof_stencil,
+        "roofline_ozaki_gram": roof_oz,
     }
     print(json.dumps(line), flush=True)
     if dist:
@@ -478,6 +487,66 @@ def roofline(pk, solver, w, dev, stream):
             "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
             "traffic": ROOFLINE_TRAFFIC_BYTES, "algorithmic_flops_per_launch": flops, "launch_ms": dur * 1e3,
             "peak_note": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)"}
+
+
+def _time_ms(fn, stream, reps):
+    import torch
+    for _ in range(3):
+        fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def roofline_stencil(pk, solver, w, dev, stream):
+    """The operator on a full n x k block: 7 FP64 operations (6 additions, one FMA) and 16 bytes per output element
+    plus 8 n bytes of diagonal; bound by the FP64 pipe (0.44 op/B is above the FP64 ridge of ~0.19)."""
+    import torch
+    f = 2 if w.dtype == "c128" else 1
+    n, k = f * w.n, f * w.k
+    g = torch.Generator(device="cpu").manual_seed(3)
+    X = torch.randn((k, n), generator=g, dtype=torch.float64).to(dev)
+    Y = torch.empty_like(X)
+    ms = _time_ms(lambda: pk.ppcg_apply_operator(solver.handle, X.data_ptr(), n, Y.data_ptr(), n, k), stream, 20)
+    ops = (14.0 if w.dtype == "c128" else 7.0) * w.n * k     # complex: both halves of a point per column
+    nbytes = 16.0 * n * k + 8.0 * n
+    ach = ops / (ms / 1e3) / 1e12
+    hbm, kind = hbm_peak()
+    return {"kernel": f"stencil_kernel: A X on {n} x {k}", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "launch_ms": ms,
+            "hbm_gbs": nbytes / (ms / 1e3) / 1e9, "hbm_frac": nbytes / (ms / 1e3) / 1e9 / hbm,
+            "peak_note": f"FP64 pipe (7 FP64 ops per output counted as flops); HBM against the {kind} copy bandwidth"}
+
+
+def roofline_ozaki(pk, solver, w, dev, stream):
+    """FP64-accurate Gram X^T W on the BF16 tensor cores (8 digit slices, 36 products): FP64-equivalent TFLOP/s and
+    the BF16 tensor work against the measured BF16 peak."""
+    import torch
+    f = 2 if w.dtype == "c128" else 1
+    n, k = f * w.n, f * w.k
+    g = torch.Generator(device="cpu").manual_seed(4)
+    A = torch.randn((k, n), generator=g, dtype=torch.float64).to(dev)
+    B = torch.randn((k, n), generator=g, dtype=torch.float64).to(dev)
+    C = torch.empty((k, k), dtype=torch.float64, device=dev)
+    ms = _time_ms(lambda: pk.ppcg_gram(solver.handle, A.data_ptr(), n, B.data_ptr(), n, k, k, C.data_ptr()),
+                  stream, 20)
+    fp64_eq = 2.0 * n * k * k / (ms / 1e3) / 1e12
+    tensor = 36 * 2.0 * n * k * k / (ms / 1e3) / 1e12
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            bf16, kind = float(json.load(fh)["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        bf16, kind = 1900.0, "fallback"
+    return {"kernel": f"Ozaki Gram (exponents + digit images + oz_img_kernel + reduce): X^T W, n={n}, {k}x{k}",
+            "bound": "tensor", "achieved": tensor, "peak": bf16, "unit": "TFLOP/s", "frac": tensor / bf16,
+            "traffic": None, "launch_ms": ms, "fp64_equivalent_tflops": fp64_eq,
+            "fp64_equivalent_vs_fp64_peak": fp64_eq / FP64_PEAK_TFLOPS,
+            "peak_note": f"{kind} dense BF16 burst peak; tensor work = 36 digit-pair products x 2 n k^2"}
 
 
 def hbm_peak():
