@@ -541,6 +541,7 @@ struct OzImgSmem {
   uint64_t empty[kSBuf];
   uint32_t tmem_slot;
   int ok;
+  int issued, consumed;
   int Ea[kM];
   int Eb[kN];
 };
@@ -581,6 +582,8 @@ __global__ void __launch_bounds__(kThreads, 1) oz_img_kernel(ImgArgs a) {
       mbar_init(smem_u32(&sm.empty[b]), 1);
     }
     sm.ok = 1;
+    sm.issued = 0;
+    sm.consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
@@ -593,7 +596,9 @@ __global__ void __launch_bounds__(kThreads, 1) oz_img_kernel(ImgArgs a) {
   const int q = warp & 3, h = warp >> 2;
   const uint8_t* srcA = a.imgA + (size_t)tm * a.nkb * kDig * kSAPlane;
   const uint8_t* srcB = a.imgB + (size_t)tn * a.nkb * kDig * kSBPlane;
-  int issued = 0;                                 // stages whose copies were issued (thread 0)
+  // Thread 0 of warp 0 produces (bulk copies into a free buffer), thread 0 of warp 1 consumes (MMAs, then a commit
+  // that frees the buffer); both run ahead independently within a chunk of kSChunkBlocks stages, and all warps meet
+  // at the chunk end to fold the group accumulators. issued / consumed live in shared memory for the timeout path.
   auto issue = [&](int st) {                      // both operands of stage st into buffer st % kSBuf
     const int b = st % kSBuf;
     const uint32_t dst = smem_u32(dyn + b * kSStage);
@@ -601,27 +606,37 @@ __global__ void __launch_bounds__(kThreads, 1) oz_img_kernel(ImgArgs a) {
     mbar_expect_tx(fb, kSStage);
     bulk_g2s(dst, srcA + (size_t)(kb0 + st) * kDig * kSAPlane, kDig * kSAPlane, fb);
     bulk_g2s(dst + kDig * kSAPlane, srcB + (size_t)(kb0 + st) * kDig * kSBPlane, kDig * kSBPlane, fb);
-    issued = st + 1;
   };
   float hi[32], lo[32];
 #pragma unroll
   for (int i = 0; i < 32; ++i) { hi[i] = 0.f; lo[i] = 0.f; }
-  if (tid == 0)
-    for (int st = 0; st < nst && st < kSBuf - 1; ++st) issue(st);
   constexpr uint32_t idesc = idesc_bf16(kM, kN);
   bool ok = true;
-  int consumed = 0;
-  for (int st = 0; st < nst; ++st) {
-    const int b = st % kSBuf;
-    const uint32_t use = (uint32_t)(st / kSBuf);
-    if (tid == 0 && sm.ok) {
-      if (!mbar_wait(smem_u32(&sm.full[b]), use & 1u)) {
-        sm.ok = 0;
-      } else {
-        consumed = st + 1;
+  int issued = 0, consumed = 0;                   // thread 0 / thread 32 only
+  for (int c0 = 0; c0 < nst; c0 += kSChunkBlocks) {
+    const int c1 = min(nst, c0 + kSChunkBlocks);
+    if (tid == 0) {
+      // keep up to kSBuf stages in flight: this chunk's and the first ones of the next
+      const int upto = min(nst, c1 + kSBuf - 1);
+      for (int st = issued; st < upto && sm.ok; ++st) {
+        if (st >= kSBuf && !mbar_wait(smem_u32(&sm.empty[st % kSBuf]), (uint32_t)((st / kSBuf - 1) & 1))) {
+          sm.ok = 0;
+          break;
+        }
+        issue(st);
+        issued = st + 1;
+        sm.issued = issued;
+      }
+    } else if (tid == 32) {
+      for (int st = c0; st < c1 && sm.ok; ++st) {
+        const int b = st % kSBuf;
+        if (!mbar_wait(smem_u32(&sm.full[b]), (uint32_t)((st / kSBuf) & 1))) {
+          sm.ok = 0;
+          break;
+        }
         tc_fence_after();
         const uint32_t a0 = smem_u32(dyn + b * kSStage), b0 = a0 + kDig * kSAPlane;
-        const bool first = (st % kSChunkBlocks) == 0;
+        const bool first = st == c0;
 #pragma unroll
         for (int g = 0; g < kGroups; ++g) {
 #pragma unroll
@@ -631,26 +646,20 @@ __global__ void __launch_bounds__(kThreads, 1) oz_img_kernel(ImgArgs a) {
           }
         }
         mma_commit(smem_u32(&sm.empty[b]));
-        const int next = st + kSBuf - 1;          // refill the buffer that stage st - 1 used
-        if (next < nst) {
-          if (next >= kSBuf) {
-            const int pb = next % kSBuf;
-            if (!mbar_wait(smem_u32(&sm.empty[pb]), (uint32_t)((next / kSBuf - 1) & 1))) sm.ok = 0;
-          }
-          if (sm.ok) issue(next);
-        }
+        consumed = st + 1;
+        sm.consumed = consumed;
       }
+      // the chunk's products are complete once its last commit has arrived
+      if (sm.ok && consumed == c1 &&
+          !mbar_wait(smem_u32(&sm.empty[(c1 - 1) % kSBuf]), (uint32_t)(((c1 - 1) / kSBuf) & 1)))
+        sm.ok = 0;
     }
-    const bool chunk_end = ((st + 1) % kSChunkBlocks) == 0 || st + 1 == nst;
-    if (chunk_end) {
-      if (tid == 0 && sm.ok && !mbar_wait(smem_u32(&sm.empty[b]), use & 1u)) sm.ok = 0;
-      __syncthreads();
-      if (!sm.ok) { ok = false; break; }
-      tc_fence_after();
-      fold_groups(tmem, q, h, hi, lo);
-      tc_fence_before();
-      __syncthreads();
-    }
+    __syncthreads();
+    if (!sm.ok) { ok = false; break; }
+    tc_fence_after();
+    fold_groups(tmem, q, h, hi, lo);
+    tc_fence_before();
+    __syncthreads();
   }
   if (ok) {
     const int ri = 32 * q + lane;
@@ -682,10 +691,10 @@ __global__ void __launch_bounds__(kThreads, 1) oz_img_kernel(ImgArgs a) {
   if (tid == 0 && !ok) {
     atomicOr(a.flag, kFlagTimeout);
     // wait (bounded) for the copies and MMAs still in flight before the CTA gives its memory back
-    for (int st = consumed; st < issued; ++st)
+    const int iss = sm.issued, con = sm.consumed;
+    for (int st = con; st < iss; ++st)
       mbar_wait(smem_u32(&sm.full[st % kSBuf]), (uint32_t)((st / kSBuf) & 1));
-    if (consumed > 0)
-      mbar_wait(smem_u32(&sm.empty[(consumed - 1) % kSBuf]), (uint32_t)(((consumed - 1) / kSBuf) & 1));
+    if (con > 0) mbar_wait(smem_u32(&sm.empty[(con - 1) % kSBuf]), (uint32_t)(((con - 1) / kSBuf) & 1));
   }
   tc_fence_before();
   __syncthreads();
