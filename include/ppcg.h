@@ -41,7 +41,7 @@ typedef enum {
   PPCG_ERR_BREAKDOWN = 5,      /* orthonormalisation failed even with shifted CholeskyQR3 */
   PPCG_ERR_NUMERIC = 6,        /* a NaN/Inf appeared in a residual norm */
   PPCG_ERR_TIMEOUT = 7,        /* a bounded device-side wait (grid barrier) gave up */
-  PPCG_ERR_UNSUPPORTED = 8     /* option valid in the paper but not provided by this build */
+  PPCG_ERR_UNSUPPORTED = 8     /* option valid in the paper but not provided by this library */
 } ppcg_status;
 
 typedef enum { PPCG_R64 = 0, PPCG_C128 = 1 } ppcg_dtype;

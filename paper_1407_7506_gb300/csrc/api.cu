@@ -572,7 +572,7 @@ const char* ppcg_status_string(ppcg_status s) {
     case PPCG_ERR_BREAKDOWN: return "PPCG_ERR_BREAKDOWN: orthonormalisation failed";
     case PPCG_ERR_NUMERIC: return "PPCG_ERR_NUMERIC: non-finite residual";
     case PPCG_ERR_TIMEOUT: return "PPCG_ERR_TIMEOUT: a bounded device wait gave up";
-    case PPCG_ERR_UNSUPPORTED: return "PPCG_ERR_UNSUPPORTED: option not provided by this build";
+    case PPCG_ERR_UNSUPPORTED: return "PPCG_ERR_UNSUPPORTED: option not provided by this library";
   }
   return "PPCG: unknown status";
 }

@@ -36,7 +36,7 @@ stencil_kernel(const double* __restrict__ X, int64_t ldx, double* __restrict__ Y
   const int64_t lm = (l > 0) ? p - plane : p + plane * (nz - 1);
   const double s = ((__ldg(x + im) + __ldg(x + ip)) + (__ldg(x + jm) + __ldg(x + jp))) +
                    (__ldg(x + lm) + __ldg(x + lp));
-  // h = 1 (every workload here) needs no scaling multiply: 6 FP64 instructions per point instead of 7
+  // h = 1 needs no scaling multiply: 6 FP64 instructions per point instead of 7
   Y[(int64_t)c * ldy + p] = fma(__ldg(dg + p), __ldg(x + p), UNIT ? -s : -inv_h2 * s);
 }
 
