@@ -48,8 +48,10 @@ __device__ bool grid_sync(unsigned* bar, unsigned nblocks, int* flag, unsigned& 
   gen += 1u;
   __syncthreads();
   if (threadIdx.x == 0) {
+    // The CTA barrier above orders every thread's writes before this release add, and release is cumulative, so
+    // they are visible at GPU scope to any CTA whose acquire load observes the count; the CTA barrier below orders
+    // that acquire before every thread's later reads.
     const unsigned target = gen * nblocks;
-    __threadfence();                                   // publish this CTA's writes at GPU scope
     red_release_gpu(bar, 1u);
     int good = 1;
     long long spins = 0;
@@ -60,7 +62,6 @@ __device__ bool grid_sync(unsigned* bar, unsigned nblocks, int* flag, unsigned& 
         break;
       }
     }
-    __threadfence();
     if (ld_relaxed_gpu(flag) & kFlagTimeout) good = 0;
     ok = good;
   }
