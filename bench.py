@@ -46,6 +46,16 @@ def _env_rank():
                                                                                                          "0"))
 
 
+def max_over_ranks(value, dist, device):
+    """The job's time is the slowest replica's: all-reduce MAX over the ranks (identity without a process group)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples every 200 ms while active."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -272,11 +282,7 @@ def main():
             wall = time.perf_counter() - t0
         if dist:
             dist.barrier()
-        ms = ev0.elapsed_time(ev1)
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
         parity = {"max_residual": float(np.max(res)), "converged": all(s_["converged"] == 1 for s_ in stats)}
         if gold is not None:
             parity["max_rel_err_vs_oracle"] = float(np.max(np.abs(lam - gold) / np.maximum(np.abs(gold), 1.0)))
@@ -425,7 +431,7 @@ def run_batched(args):
         ev1.record()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev) / args.steps
     # the same batch one problem at a time, for the concurrency gain (outside the timed region)
     t1 = time.perf_counter()
     bs.solve(X0s, tol=1e-8, max_concurrent=1)
