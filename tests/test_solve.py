@@ -225,6 +225,30 @@ def test_solve_config2_full_size():
         assert np.all(_rel(lam, gold) <= LAM_TOL), np.max(_rel(lam, gold))
 
 
+@pytest.mark.slow
+def test_config3_size_mixed_form_against_separable_spectrum():
+    # the config-3 shape and form (48^3, k = 1024, sbsize = 8, TF32 projections, FP64-accurate GEMMs otherwise)
+    # with a separable potential, whose spectrum is known exactly: sums of three 1-D spectra
+    N, k, q = 48, 1024, 8
+    w = wl.small("sep48", N=N, k=k, sbsize=q, potential="separable", seed=1003)
+    V, X0 = wl.make_inputs(w)
+    Vg = V.reshape((N, N, N), order="F")
+    v1, v2, v3 = Vg[:, 0, 0] - Vg[0, 0, 0], Vg[0, :, 0] - Vg[0, 0, 0], Vg[0, 0, :]   # V = v1(i) + v2(j) + v3(l)
+    np.testing.assert_allclose(Vg, v1[:, None, None] + v2[None, :, None] + v3[None, None, :], atol=1e-14)
+    L = 2 * np.eye(N) - np.roll(np.eye(N), 1, 0) - np.roll(np.eye(N), -1, 0)      # periodic 1-D second difference
+    mus = [np.linalg.eigvalsh(L + np.diag(v)) for v in (v1, v2, v3)]
+    exact = np.sort((mus[0][:, None, None] + mus[1][None, :, None] + mus[2][None, None, :]).ravel())[:k + 1]
+    lam, X, res, st = _gpu_solve(V, N, k, q, 5, X0, precision="mixed", fp64_gemm="ozaki", maxiter=4000)
+    assert st["status"] == "ok" and st["converged"] == 1, st
+    assert np.all(_rel(lam, exact[:k]) <= 1e-9), np.max(_rel(lam, exact[:k]))
+    cols = np.random.default_rng(1).choice(k, 32, replace=False)
+    r = np.linalg.norm(oracle.apply_H(V, N, 1.0, X[:, cols]) - X[:, cols] * lam[cols], axis=0)
+    assert np.max(r) <= 1e-8 * (1 + 1e-6)
+    Xs = X[:, cols]
+    np.testing.assert_allclose(Xs.T @ Xs, np.eye(len(cols)), atol=1e-12)
+    np.testing.assert_allclose(res[cols], r, rtol=1e-3, atol=1e-13)
+
+
 # ------------------------------------------------------------------------------------- edge cases
 def test_maxiter_one_returns_last_ritz_pairs():
     N, k = 7, 6
