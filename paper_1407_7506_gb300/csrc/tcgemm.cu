@@ -3,12 +3,15 @@
 // Gram of the first CholeskyQR pass (its error changes only the conditioning of R, not span(X), because
 // X R^{-1} is applied in FP64). This is the mixed-precision form of the method's workload.
 //
-// The blocks are FP64 in HBM, which TMA cannot convert, so the operand tiles are staged by the threads: coalesced
-// FP64 loads, conversion to TF32 (round to nearest), and stores into shared memory in the canonical K-major
-// layout without swizzle (core matrices of 8 rows x 16 bytes; LBO = 128 B between core matrices along K,
-// SBO = 1024 B between 8-row groups). One thread issues tcgen05.mma (M = 128, N = NT, K = 8 per instruction) into
-// a TMEM accumulator and commits to an mbarrier per stage; two stages overlap staging with the MMAs. The epilogue
-// reads TMEM with tcgen05.ld (each warp its 32-lane quadrant) and writes FP64.
+// The blocks are FP64 in HBM, which TMA cannot convert, so the operand tiles are staged by the threads: FP64
+// loads, conversion to TF32 (round to nearest), and stores into shared memory in the K-major layout with the
+// 128-byte swizzle: a stage holds K = 32 TF32 values (128 B) per tile row, rows 128 B apart, and the 16-byte chunk
+// c of row r sits at chunk position c ^ (r mod 8). The swizzle is what lets the loads follow the FP64 data: a warp
+// reads 32 consecutive elements of one column (256 contiguous bytes, two cache lines per request) and still writes
+// 32 distinct banks. One thread issues tcgen05.mma (M = 128, N = NT, K = 8 per instruction, the descriptor start
+// advanced by 32 B inside the 128-byte atom) into a TMEM accumulator and commits to an mbarrier per stage; two
+// stages overlap staging with the MMAs. The epilogue reads TMEM with tcgen05.ld (each warp its 32-lane quadrant)
+// and writes FP64.
 //
 //   tc_gram    C = A^T B split over row chunks into FP64 partials (summed by the FP64 Gram reduce kernel)
 //   tc_update  Y = Y - A G (or Y = A G)
@@ -31,21 +34,25 @@ namespace {
 using namespace tc;
 
 constexpr int kM = 128;           // MMA M: rows of the accumulator = TMEM lanes
-constexpr int kBK = 32;           // K elements staged per stage (4 MMAs of K = 8)
+constexpr int kBK = 32;           // K elements staged per stage (4 MMAs of K = 8): one 128-byte swizzle atom
 constexpr int kThreads = 256;     // 8 warps
-constexpr uint32_t kLBO = 128;    // bytes between core matrices along K
-constexpr uint32_t kSBO = 1024;   // bytes between 8-row groups (kBK / 4 core matrices of 128 B)
+constexpr uint32_t kRowB = 128;   // bytes per tile row (kBK TF32 values)
+constexpr uint32_t kSBO = 1024;   // bytes between 8-row groups
 
+// byte offset of element (row, k) of a stage tile: row-major 128-byte rows, 16-byte chunks XOR-swizzled by row mod 8
 __device__ __forceinline__ uint32_t tile_off(int row, int k) {
-  return (uint32_t)(row >> 3) * kSBO + (uint32_t)(row & 7) * 16u + (uint32_t)(k >> 2) * kLBO + (uint32_t)(k & 3) * 4u;
+  return (uint32_t)row * kRowB + ((uint32_t)((k >> 2) ^ (row & 7)) << 4) + (uint32_t)(k & 3) * 4u;
 }
 
+// shared-memory descriptor of a K-major tile with the 128-byte swizzle (layout code 2 in bits 61-63); the tile is
+// 1024-byte aligned, so the base offset is 0, and the leading byte offset is unused for this layout
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((kLBO >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)1 << 16;
   d |= (uint64_t)((kSBO >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;          // descriptor version of tcgen05; base offset 0; no swizzle
+  d |= (uint64_t)1 << 46;          // descriptor version of tcgen05
+  d |= (uint64_t)2 << 61;          // 128-byte swizzle
   return d;
 }
 
@@ -53,11 +60,34 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ float to_tf32(double x) {
-  uint32_t r;
-  const float f = (float)x;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
-  return __uint_as_float(r);
+// FP32 bit pattern of the TF32 value nearest to the double whose upper 32-bit word is hi, ties away from zero (the
+// rounding of cvt.rna.tf32). The upper word holds the sign, the exponent and the leading 20 mantissa bits: the 10
+// that TF32 keeps and the first one it drops, which alone decides this rounding. The exponent is rebiased in place
+// (1023 -> 127) with integer operations only, so the conversion stays off GB300's narrow FP64 pipe. Magnitudes below
+// the FP32 normal range become zero and magnitudes above it infinity; a NaN whose payload lies only in the low word
+// becomes infinity (the result is non-finite either way).
+__device__ __forceinline__ uint32_t tf32_from_hi(uint32_t hi) {
+  const uint32_t mag = hi & 0x7FFFFFFFu;
+  uint32_t f = (((mag - 0x38000000u) << 3) + 0x1000u) & 0xFFFFE000u;
+  if (mag < 0x38100000u) f = 0u;
+  if (mag >= 0x47F00000u) f = mag > 0x7FF00000u ? 0x7FC00000u : 0x7F800000u;
+  return f | (hi & 0x80000000u);
+}
+
+// upper 32-bit word of a double in global memory (little-endian: at byte offset 4)
+__device__ __forceinline__ uint32_t ld_hi(const double* p) {
+  return __ldg(reinterpret_cast<const uint32_t*>(p) + 1);
+}
+
+// exact FP32 -> FP64 widening by integer field moves (FP32 subnormals, far below any accumulated value here, become
+// zero; infinities and NaNs stay so)
+__device__ __forceinline__ double widen(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const uint32_t e = (b >> 23) & 0xFFu;
+  const uint32_t eo = e == 0xFFu ? 0x7FFu : e + 896u;
+  const uint32_t hi = e == 0u ? (b & 0x80000000u) : ((b & 0x80000000u) | (eo << 20) | ((b & 0x7FFFFFu) >> 3));
+  const uint32_t lo = e == 0u ? 0u : (b << 29);
+  return __hiloint2double((int)hi, (int)lo);
 }
 
 struct TcSmem {
@@ -95,7 +125,7 @@ __device__ bool tc_mainloop(int nk, uint8_t* tiles, uint32_t a_bytes, uint32_t b
       const uint32_t a0 = smem_u32(a_tile), b0 = smem_u32(b_tile);
 #pragma unroll
       for (int j = 0; j < kBK / 8; ++j)
-        mma_tf32(tmem, smem_desc(a0 + j * 2 * kLBO), smem_desc(b0 + j * 2 * kLBO), idesc,
+        mma_tf32(tmem, smem_desc(a0 + j * 32), smem_desc(b0 + j * 32), idesc,
                  (kb > 0 || j > 0) ? 1u : 0u);
       mma_commit(smem_u32(&sm.mbar[s]));
     }
@@ -140,16 +170,20 @@ __device__ void tc_teardown(TcSmem& sm, uint32_t tmem, uint32_t ncols, bool ok, 
   }
 }
 
-// Per-thread register staging. A warp stages whole core matrices (8 rows x 4 k = 32 elements, one per lane), so
-// its shared-memory stores fill 128 contiguous bytes. All global loads of a stage are issued before any is
-// converted and stored, and the next stage's loads are issued while the MMAs run.
+// Per-thread register staging: all global loads of a stage are issued before any is converted and stored, and the
+// next stage's loads are issued while the MMAs run.
 template <int NT>
 struct Stage {
-  static constexpr int kA = (kM / 8) * (kBK / 4) / (kThreads / 32);   // core matrices of A per warp (16)
-  static constexpr int kB = (NT / 8) * (kBK / 4) / (kThreads / 32);   // core matrices of B per warp
-  double a[kA];
-  double b[kB];
+  static constexpr int kA = kM * kBK / kThreads;    // elements of A per thread (16)
+  static constexpr int kB = NT * kBK / kThreads;    // elements of B per thread
+  uint32_t a[kA];   // upper words of the FP64 elements
+  uint32_t b[kB];
 };
+
+// 1024-byte aligned start of the stage tiles inside the dynamic shared memory (its size includes 1024 B of slack)
+__device__ __forceinline__ uint8_t* align_tiles(uint8_t* dyn) {
+  return dyn + ((1024u - (smem_u32(dyn) & 1023u)) & 1023u);
+}
 
 // ------------------------------------------------------------------------------------------ C = A^T B partials
 // grid (tiles_m * tiles_n, nsplit); tile rows m0 = tm * 128 (columns of A), cols n0 = tn * NT (columns of B)
@@ -164,47 +198,36 @@ tc_gram_kernel(const double* __restrict__ A, int64_t lda, const double* __restri
   const int64_t r_begin = (int64_t)blockIdx.y * rows_per_split;
   const int64_t r_end = min(n, r_begin + rows_per_split);
   const int nk = r_end > r_begin ? (int)ceil_div(r_end - r_begin, kBK) : 0;
-  constexpr uint32_t a_bytes = (kM / 8) * kSBO, b_bytes = (uint32_t)(NT / 8) * kSBO;
+  constexpr uint32_t a_bytes = kM * kRowB, b_bytes = (uint32_t)NT * kRowB;
   constexpr uint32_t ncols = (uint32_t)NT;
   tc_setup(sm, ncols);
   const uint32_t tmem = sm.tmem_slot;
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
-  const int mm = lane >> 2, kk = lane & 3;        // position inside a core matrix (8 rows x 4 k)
+  // lane = k (a row of A and B), warp w takes tile rows w, w + 8, ...: 256 contiguous bytes per warp load
   Stage<NT> reg;
   auto load = [&](int kb) {
-    const int64_t gr = r_begin + (int64_t)kb * kBK;
+    const int64_t r = r_begin + (int64_t)kb * kBK + lane;
+    const bool rin = r < r_end;
 #pragma unroll
     for (int i = 0; i < Stage<NT>::kA; ++i) {
-      const int cm = warp + i * (kThreads / 32);
-      const int g = cm / (kBK / 4), c = cm % (kBK / 4);
-      const int64_t r = gr + 4 * c + kk;
-      const int col = m0 + 8 * g + mm;
-      reg.a[i] = (r < r_end && col < ma) ? __ldg(A + r + (int64_t)col * lda) : 0.0;
+      const int col = m0 + warp + 8 * i;
+      reg.a[i] = (rin && col < ma) ? ld_hi(A + r + (int64_t)col * lda) : 0u;
     }
 #pragma unroll
     for (int i = 0; i < Stage<NT>::kB; ++i) {
-      const int cm = warp + i * (kThreads / 32);
-      const int g = cm / (kBK / 4), c = cm % (kBK / 4);
-      const int64_t r = gr + 4 * c + kk;
-      const int col = n0 + 8 * g + mm;
-      reg.b[i] = (r < r_end && col < mb) ? __ldg(B + r + (int64_t)col * ldb) : 0.0;
+      const int col = n0 + warp + 8 * i;
+      reg.b[i] = (rin && col < mb) ? ld_hi(B + r + (int64_t)col * ldb) : 0u;
     }
   };
   auto store = [&](uint8_t* a_tile, uint8_t* b_tile) {
 #pragma unroll
-    for (int i = 0; i < Stage<NT>::kA; ++i) {
-      const int cm = warp + i * (kThreads / 32);
-      const int g = cm / (kBK / 4), c = cm % (kBK / 4);
-      *reinterpret_cast<float*>(a_tile + tile_off(8 * g + mm, 4 * c + kk)) = to_tf32(reg.a[i]);
-    }
+    for (int i = 0; i < Stage<NT>::kA; ++i)
+      *reinterpret_cast<uint32_t*>(a_tile + tile_off(warp + 8 * i, lane)) = tf32_from_hi(reg.a[i]);
 #pragma unroll
-    for (int i = 0; i < Stage<NT>::kB; ++i) {
-      const int cm = warp + i * (kThreads / 32);
-      const int g = cm / (kBK / 4), c = cm % (kBK / 4);
-      *reinterpret_cast<float*>(b_tile + tile_off(8 * g + mm, 4 * c + kk)) = to_tf32(reg.b[i]);
-    }
+    for (int i = 0; i < Stage<NT>::kB; ++i)
+      *reinterpret_cast<uint32_t*>(b_tile + tile_off(warp + 8 * i, lane)) = tf32_from_hi(reg.b[i]);
   };
-  const bool ok = tc_mainloop(nk, dyn, a_bytes, b_bytes, sm, tmem, idesc_tf32(kM, NT), load, store);
+  const bool ok = tc_mainloop(nk, align_tiles(dyn), a_bytes, b_bytes, sm, tmem, idesc_tf32(kM, NT), load, store);
   if (ok) {
     // epilogue: warp w reads lanes 32 (w % 4).., columns [h NT/2, (h+1) NT/2) with h = w / 4
     double* out = part + (int64_t)blockIdx.y * ma * mb;
@@ -222,7 +245,7 @@ tc_gram_kernel(const double* __restrict__ A, int64_t lda, const double* __restri
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int gj = n0 + c0 + i;
-          if (gj < mb) out[gi + (int64_t)gj * ma] = (double)v[i];
+          if (gj < mb) out[gi + (int64_t)gj * ma] = widen(v[i]);
         }
       }
     }
@@ -241,48 +264,51 @@ tc_update_kernel(const double* __restrict__ A, int64_t lda, const double* __rest
   const int64_t r0 = (int64_t)blockIdx.x * kM;
   const int c0 = blockIdx.y * NT;
   const int nk = (int)ceil_div(m, kBK);
-  constexpr uint32_t a_bytes = (kM / 8) * kSBO, b_bytes = (uint32_t)(NT / 8) * kSBO;
+  constexpr uint32_t a_bytes = kM * kRowB, b_bytes = (uint32_t)NT * kRowB;
   constexpr uint32_t ncols = (uint32_t)NT;
   tc_setup(sm, ncols);
   const uint32_t tmem = sm.tmem_slot;
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
-  const int ar = lane & 7, ak = lane >> 3;        // A: lanes run down the rows (coalesced in X)
-  const int bn = lane >> 2, bk = lane & 3;        // B: lanes run along k (contiguous in G)
+  // A: thread items (row, 4-element chunk of k); lanes run down 32 consecutive rows of X (256 contiguous bytes per
+  // load) and each item is one 16-byte store, conflict-free under the swizzle. B (G, contiguous along k): lane = k.
   Stage<NT> reg;
   auto load = [&](int kb) {
     const int k0 = kb * kBK;
 #pragma unroll
-    for (int i = 0; i < Stage<NT>::kA; ++i) {
-      const int cm = warp + i * (kThreads / 32);
-      const int g = cm % (kM / 8), c = cm / (kM / 8);
-      const int64_t gr = r0 + 8 * g + ar;
-      const int gk = k0 + 4 * c + ak;
-      reg.a[i] = (gr < n && gk < m) ? __ldg(A + gr + (int64_t)gk * lda) : 0.0;
+    for (int i = 0; i < Stage<NT>::kA / 4; ++i) {
+      const int it = threadIdx.x + kThreads * i;
+      const int row = it % kM, c = it / kM;
+      const int64_t gr = r0 + row;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int gk = k0 + 4 * c + j;
+        reg.a[4 * i + j] = (gr < n && gk < m) ? ld_hi(A + gr + (int64_t)gk * lda) : 0u;
+      }
     }
+    const int gk = k0 + lane;
 #pragma unroll
     for (int i = 0; i < Stage<NT>::kB; ++i) {
-      const int cm = warp + i * (kThreads / 32);
-      const int g = cm / (kBK / 4), c = cm % (kBK / 4);
-      const int gk = k0 + 4 * c + bk;
-      const int gc = c0 + 8 * g + bn;
-      reg.b[i] = (gk < m && gc < p) ? __ldg(G + gk + (int64_t)gc * ldg) : 0.0;
+      const int gc = c0 + warp + 8 * i;
+      reg.b[i] = (gk < m && gc < p) ? ld_hi(G + gk + (int64_t)gc * ldg) : 0u;
     }
   };
   auto store = [&](uint8_t* a_tile, uint8_t* b_tile) {
 #pragma unroll
-    for (int i = 0; i < Stage<NT>::kA; ++i) {
-      const int cm = warp + i * (kThreads / 32);
-      const int g = cm % (kM / 8), c = cm / (kM / 8);
-      *reinterpret_cast<float*>(a_tile + tile_off(8 * g + ar, 4 * c + ak)) = to_tf32(reg.a[i]);
+    for (int i = 0; i < Stage<NT>::kA / 4; ++i) {
+      const int it = threadIdx.x + kThreads * i;
+      const int row = it % kM, c = it / kM;
+      uint4 v;
+      v.x = tf32_from_hi(reg.a[4 * i + 0]);
+      v.y = tf32_from_hi(reg.a[4 * i + 1]);
+      v.z = tf32_from_hi(reg.a[4 * i + 2]);
+      v.w = tf32_from_hi(reg.a[4 * i + 3]);
+      *reinterpret_cast<uint4*>(a_tile + tile_off(row, 4 * c)) = v;
     }
 #pragma unroll
-    for (int i = 0; i < Stage<NT>::kB; ++i) {
-      const int cm = warp + i * (kThreads / 32);
-      const int g = cm / (kBK / 4), c = cm % (kBK / 4);
-      *reinterpret_cast<float*>(b_tile + tile_off(8 * g + bn, 4 * c + bk)) = to_tf32(reg.b[i]);
-    }
+    for (int i = 0; i < Stage<NT>::kB; ++i)
+      *reinterpret_cast<uint32_t*>(b_tile + tile_off(warp + 8 * i, lane)) = tf32_from_hi(reg.b[i]);
   };
-  const bool ok = tc_mainloop(nk, dyn, a_bytes, b_bytes, sm, tmem, idesc_tf32(kM, NT), load, store);
+  const bool ok = tc_mainloop(nk, align_tiles(dyn), a_bytes, b_bytes, sm, tmem, idesc_tf32(kM, NT), load, store);
   if (ok) {
     const int q = warp & 3, h = warp >> 2;
     const int64_t gr = r0 + 32 * q + lane;
@@ -303,7 +329,7 @@ tc_update_kernel(const double* __restrict__ A, int64_t lda, const double* __rest
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int gc = c0 + cc + i;
-          if (gc < p) Y[gr + (int64_t)gc * ldy] = subtract ? (y[i] - (double)v[i]) : (double)v[i];
+          if (gc < p) Y[gr + (int64_t)gc * ldy] = subtract ? (y[i] - widen(v[i])) : widen(v[i]);
         }
       }
     }
@@ -318,7 +344,7 @@ int pick_nt(int cols) {
   return 256;
 }
 
-size_t tc_smem_bytes(int NT) { return 2 * ((size_t)(kM / 8) * kSBO + (size_t)(NT / 8) * kSBO) + 1024; }
+size_t tc_smem_bytes(int NT) { return 2 * ((size_t)kM * kRowB + (size_t)NT * kRowB) + 1024; }
 
 // Sets the dynamic shared memory of fn to at least `bytes`, padded so that no more CTAs than 512 / NT can be
 // resident on one SM: tcgen05.alloc waits for free TMEM columns, and the SM has 512.
