@@ -4,16 +4,16 @@
 // X R^{-1} is applied in FP64). This is the mixed-precision form of the method's workload.
 //
 // The blocks are FP64 in HBM, which TMA cannot convert, so the operand tiles are staged by the threads: FP64
-// loads, conversion to TF32 (round to nearest), and stores into shared memory in the K-major layout with the
+// loads, conversion to TF32 (round to nearest, by integer operations on the upper word), and stores into shared memory in the K-major layout with the
 // 128-byte swizzle: a stage holds K = 32 TF32 values (128 B) per tile row, rows 128 B apart, and the 16-byte chunk
 // c of row r sits at chunk position c ^ (r mod 8). The swizzle is what lets the loads follow the FP64 data: a warp
 // reads 32 consecutive elements of one column (256 contiguous bytes, two cache lines per request) and still writes
 // 32 distinct banks. One thread issues tcgen05.mma (M = 128, N = NT, K = 8 per instruction, the descriptor start
 // advanced by 32 B inside the 128-byte atom) into a TMEM accumulator and commits to an mbarrier per stage; two
-// stages overlap staging with the MMAs. The epilogue reads TMEM with tcgen05.ld (each warp its 32-lane quadrant)
-// and writes FP64.
+// stages overlap staging with the MMAs. The epilogue reads TMEM with tcgen05.ld (each warp its 32-lane quadrant);
+// the Gram writes FP32 partials, the update subtracts in FP64.
 //
-//   tc_gram    C = A^T B split over row chunks into FP64 partials (summed by the FP64 Gram reduce kernel)
+//   tc_gram    C = A^T B split over row chunks into FP32 partials, summed in FP32 by tc_reduce_kernel and widened
 //   tc_update  Y = Y - A G (or Y = A G)
 //
 // Every mbarrier wait is bounded; on timeout the CTA records kFlagTimeout, waits (bounded) once more for its
@@ -25,17 +25,14 @@
 
 namespace ppcg {
 
-// FP64 Gram reduce kernel launcher (gemm.cu)
-cudaError_t gram_reduce_partials(const double* part, int nsplit, int ma, int mb, double* C, int ldc, bool symmetric,
-                                 cudaStream_t s);
-
 namespace {
 
 using namespace tc;
 
 constexpr int kM = 128;           // MMA M: rows of the accumulator = TMEM lanes
 constexpr int kBK = 32;           // K elements staged per stage (4 MMAs of K = 8): one 128-byte swizzle atom
-constexpr int kThreads = 256;     // 8 warps
+constexpr int kThreads = 512;     // 16 warps: 4 per scheduler, to hide the latency of the integer conversions
+constexpr int kWarps = kThreads / 32;
 constexpr uint32_t kRowB = 128;   // bytes per tile row (kBK TF32 values)
 constexpr uint32_t kSBO = 1024;   // bytes between 8-row groups
 
@@ -96,28 +93,31 @@ struct TcSmem {
   int ok;
 };
 
-// Shared machinery: K loop over nk stages of kBK. `load(kb)` issues the global loads of stage kb into registers,
-// `store(a_tile, b_tile)` converts and writes them; thread 0 issues the MMAs. The loads of stage kb+1 are in flight
-// while stage kb's MMAs are issued and while the loop waits for the buffer it is about to overwrite.
+// Shared machinery: K loop over nk stages of kBK. `load(kb, r)` issues the global loads of stage kb into the
+// register set r, `store(a_tile, b_tile, r)` converts r and writes the stage tiles; thread 0 issues the MMAs. Two
+// register sets alternate, and the loads of stage kb+1 are issued before stage kb is converted, so their memory
+// latency overlaps the conversion, the barrier and the MMA issue of stage kb.
 // Returns false (uniformly) if a bounded wait gave up; TMEM is still allocated on return (caller frees it).
-template <class LoadFn, class StoreFn>
+// The A tile has MT halves of 128 rows, each with its own accumulator of NT TMEM columns (at column h NT), and
+// every staged B tile feeds all of them.
+template <class Regs, int MT, int NT, class LoadFn, class StoreFn>
 __device__ bool tc_mainloop(int nk, uint8_t* tiles, uint32_t a_bytes, uint32_t b_bytes, TcSmem& sm, uint32_t tmem,
                             uint32_t idesc, LoadFn load, StoreFn store) {
   const int tid = threadIdx.x;
   const uint32_t stage_bytes = a_bytes + b_bytes;
-  if (nk > 0) load(0);
-  for (int kb = 0; kb < nk; ++kb) {
+  Regs r0, r1;
+  auto step = [&](int kb, Regs& cur, Regs& nxt) -> bool {
     const int s = kb & 1;
     uint8_t* a_tile = tiles + s * stage_bytes;
     uint8_t* b_tile = a_tile + a_bytes;
+    if (kb + 1 < nk) load(kb + 1, nxt);
     if (kb >= 2) {
       // the MMAs of step kb-2 used this stage: wait for their commit (completion number (kb-2)/2)
       if (tid == 0) sm.ok = mbar_wait(smem_u32(&sm.mbar[s]), (uint32_t)(((kb - 2) >> 1) & 1)) ? 1 : 0;
       __syncthreads();
       if (!sm.ok) return false;
     }
-    store(a_tile, b_tile);
-    if (kb + 1 < nk) load(kb + 1);
+    store(a_tile, b_tile, cur);
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
@@ -125,10 +125,18 @@ __device__ bool tc_mainloop(int nk, uint8_t* tiles, uint32_t a_bytes, uint32_t b
       const uint32_t a0 = smem_u32(a_tile), b0 = smem_u32(b_tile);
 #pragma unroll
       for (int j = 0; j < kBK / 8; ++j)
-        mma_tf32(tmem, smem_desc(a0 + j * 32), smem_desc(b0 + j * 32), idesc,
-                 (kb > 0 || j > 0) ? 1u : 0u);
+#pragma unroll
+        for (int h = 0; h < MT; ++h)
+          mma_tf32(tmem + (uint32_t)(h * NT), smem_desc(a0 + h * kM * kRowB + j * 32), smem_desc(b0 + j * 32), idesc,
+                   (kb > 0 || j > 0) ? 1u : 0u);
       mma_commit(smem_u32(&sm.mbar[s]));
     }
+    return true;
+  };
+  if (nk > 0) load(0, r0);
+  for (int kb = 0; kb < nk; kb += 2) {
+    if (!step(kb, r0, r1)) return false;
+    if (kb + 1 < nk && !step(kb + 1, r1, r0)) return false;
   }
   if (nk > 0) {
     const int last = nk - 1;
@@ -172,9 +180,9 @@ __device__ void tc_teardown(TcSmem& sm, uint32_t tmem, uint32_t ncols, bool ok, 
 
 // Per-thread register staging: all global loads of a stage are issued before any is converted and stored, and the
 // next stage's loads are issued while the MMAs run.
-template <int NT>
+template <int NT, int MT>
 struct Stage {
-  static constexpr int kA = kM * kBK / kThreads;    // elements of A per thread (16)
+  static constexpr int kA = MT * kM * kBK / kThreads;    // elements of A per thread
   static constexpr int kB = NT * kBK / kThreads;    // elements of B per thread
   uint32_t a[kA];   // upper words of the FP64 elements
   uint32_t b[kB];
@@ -186,66 +194,69 @@ __device__ __forceinline__ uint8_t* align_tiles(uint8_t* dyn) {
 }
 
 // ------------------------------------------------------------------------------------------ C = A^T B partials
-// grid (tiles_m * tiles_n, nsplit); tile rows m0 = tm * 128 (columns of A), cols n0 = tn * NT (columns of B)
-template <int NT>
+// grid (tiles_m * tiles_n, nsplit); tile rows m0 = tm * 128 MT (columns of A), cols n0 = tn * NT (columns of B)
+template <int NT, int MT>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_gram_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ B, int64_t ldb, int64_t n,
-               int ma, int mb, int tiles_n, int64_t rows_per_split, double* __restrict__ part, int* flag) {
+               int ma, int mb, int tiles_n, int64_t rows_per_split, float* __restrict__ part, int* flag) {
+  using Regs = Stage<NT, MT>;
   extern __shared__ __align__(1024) uint8_t dyn[];
   __shared__ TcSmem sm;
   const int tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
-  const int m0 = tm * kM, n0 = tn * NT;
+  const int m0 = tm * kM * MT, n0 = tn * NT;
   const int64_t r_begin = (int64_t)blockIdx.y * rows_per_split;
   const int64_t r_end = min(n, r_begin + rows_per_split);
   const int nk = r_end > r_begin ? (int)ceil_div(r_end - r_begin, kBK) : 0;
-  constexpr uint32_t a_bytes = kM * kRowB, b_bytes = (uint32_t)NT * kRowB;
-  constexpr uint32_t ncols = (uint32_t)NT;
+  constexpr uint32_t a_bytes = MT * kM * kRowB, b_bytes = (uint32_t)NT * kRowB;
+  constexpr uint32_t ncols = (uint32_t)(MT * NT);
   tc_setup(sm, ncols);
   const uint32_t tmem = sm.tmem_slot;
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
-  // lane = k (a row of A and B), warp w takes tile rows w, w + 8, ...: 256 contiguous bytes per warp load
-  Stage<NT> reg;
-  auto load = [&](int kb) {
+  // lane = k (a row of A and B), warp w takes tile rows w, w + 16, ...: 256 contiguous bytes per warp load
+  auto load = [&](int kb, Regs& reg) {
     const int64_t r = r_begin + (int64_t)kb * kBK + lane;
     const bool rin = r < r_end;
 #pragma unroll
-    for (int i = 0; i < Stage<NT>::kA; ++i) {
-      const int col = m0 + warp + 8 * i;
+    for (int i = 0; i < Regs::kA; ++i) {
+      const int col = m0 + warp + kWarps * i;
       reg.a[i] = (rin && col < ma) ? ld_hi(A + r + (int64_t)col * lda) : 0u;
     }
 #pragma unroll
-    for (int i = 0; i < Stage<NT>::kB; ++i) {
-      const int col = n0 + warp + 8 * i;
+    for (int i = 0; i < Regs::kB; ++i) {
+      const int col = n0 + warp + kWarps * i;
       reg.b[i] = (rin && col < mb) ? ld_hi(B + r + (int64_t)col * ldb) : 0u;
     }
   };
-  auto store = [&](uint8_t* a_tile, uint8_t* b_tile) {
+  auto store = [&](uint8_t* a_tile, uint8_t* b_tile, const Regs& reg) {
 #pragma unroll
-    for (int i = 0; i < Stage<NT>::kA; ++i)
-      *reinterpret_cast<uint32_t*>(a_tile + tile_off(warp + 8 * i, lane)) = tf32_from_hi(reg.a[i]);
+    for (int i = 0; i < Regs::kA; ++i)
+      *reinterpret_cast<uint32_t*>(a_tile + tile_off(warp + kWarps * i, lane)) = tf32_from_hi(reg.a[i]);
 #pragma unroll
-    for (int i = 0; i < Stage<NT>::kB; ++i)
-      *reinterpret_cast<uint32_t*>(b_tile + tile_off(warp + 8 * i, lane)) = tf32_from_hi(reg.b[i]);
+    for (int i = 0; i < Regs::kB; ++i)
+      *reinterpret_cast<uint32_t*>(b_tile + tile_off(warp + kWarps * i, lane)) = tf32_from_hi(reg.b[i]);
   };
-  const bool ok = tc_mainloop(nk, align_tiles(dyn), a_bytes, b_bytes, sm, tmem, idesc_tf32(kM, NT), load, store);
+  const bool ok = tc_mainloop<Regs, MT, NT>(nk, align_tiles(dyn), a_bytes, b_bytes, sm, tmem, idesc_tf32(kM, NT),
+                                            load, store);
   if (ok) {
-    // epilogue: warp w reads lanes 32 (w % 4).., columns [h NT/2, (h+1) NT/2) with h = w / 4
-    double* out = part + (int64_t)blockIdx.y * ma * mb;
+    // epilogue: warp w reads TMEM lanes 32 (w % 4).. (its quadrant) of every half, 16-column chunks w / 4, + 4, ...
+    float* out = part + (int64_t)blockIdx.y * ma * mb;
     const int q = warp & 3, h = warp >> 2;
-    const int row = 32 * q + lane;
-    const int gi = m0 + row;
 #pragma unroll 1
-    for (int c0 = h * (NT / 2); c0 < (h + 1) * (NT / 2); c0 += 16) {
-      float v[16];
-      if (nk > 0) tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
-      else
+    for (int half = 0; half < MT; ++half) {
+      const int gi = m0 + half * kM + 32 * q + lane;
+#pragma unroll 1
+      for (int c0 = 16 * h; c0 < NT; c0 += 16 * (kWarps / 4)) {
+        float v[16];
+        if (nk > 0) tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(half * NT + c0), v);
+        else
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = 0.f;
-      if (gi < ma) {
+          for (int i = 0; i < 16; ++i) v[i] = 0.f;
+        if (gi < ma) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int gj = n0 + c0 + i;
-          if (gj < mb) out[gi + (int64_t)gj * ma] = widen(v[i]);
+          for (int i = 0; i < 16; ++i) {
+            const int gj = n0 + c0 + i;
+            if (gj < mb) out[gi + (int64_t)gj * ma] = v[i];
+          }
         }
       }
     }
@@ -253,31 +264,51 @@ tc_gram_kernel(const double* __restrict__ A, int64_t lda, const double* __restri
   tc_teardown(sm, tmem, ncols, ok, nk, flag);
 }
 
+// C = sum over the nsplit FP32 partials, summed in FP32 (their rounding, ~nsplit 2^-24 relative, is far below the
+// 2^-11 of the TF32 inputs) and widened to FP64; a symmetric C takes its lower triangle from the upper one.
+__global__ void tc_reduce_kernel(const float* __restrict__ part, int nsplit, int ma, int mb, double* __restrict__ C,
+                                 int ldc, int symmetric) {
+  const int64_t total = (int64_t)ma * mb;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % ma), j = (int)(e / ma);
+    const int64_t o = (symmetric && i > j) ? j + (int64_t)i * ma : e;
+    float s0 = 0.f, s1 = 0.f;
+    int q = 0;
+    for (; q + 1 < nsplit; q += 2) {
+      s0 += __ldg(part + (int64_t)q * total + o);
+      s1 += __ldg(part + (int64_t)(q + 1) * total + o);
+    }
+    if (q < nsplit) s0 += __ldg(part + (int64_t)q * total + o);
+    C[i + (int64_t)j * ldc] = widen(s0 + s1);
+  }
+}
+
 // ------------------------------------------------------------------------------------------ Y = Y - A G / Y = A G
-// grid (ceil(n / 128), ceil(p / NT)); A: n x m, G: m x p, Y: n x p
-template <int NT>
+// grid (ceil(n / (128 MT)), ceil(p / NT)); A: n x m, G: m x p, Y: n x p
+template <int NT, int MT>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_update_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ G, int ldg, int64_t n, int m,
                  int p, double* Y, int64_t ldy, int subtract, int* flag) {
+  using Regs = Stage<NT, MT>;
   extern __shared__ __align__(1024) uint8_t dyn[];
   __shared__ TcSmem sm;
-  const int64_t r0 = (int64_t)blockIdx.x * kM;
+  const int64_t r0 = (int64_t)blockIdx.x * kM * MT;
   const int c0 = blockIdx.y * NT;
   const int nk = (int)ceil_div(m, kBK);
-  constexpr uint32_t a_bytes = kM * kRowB, b_bytes = (uint32_t)NT * kRowB;
-  constexpr uint32_t ncols = (uint32_t)NT;
+  constexpr uint32_t a_bytes = MT * kM * kRowB, b_bytes = (uint32_t)NT * kRowB;
+  constexpr uint32_t ncols = (uint32_t)(MT * NT);
+  constexpr int kRows = MT * kM;
   tc_setup(sm, ncols);
   const uint32_t tmem = sm.tmem_slot;
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   // A: thread items (row, 4-element chunk of k); lanes run down 32 consecutive rows of X (256 contiguous bytes per
   // load) and each item is one 16-byte store, conflict-free under the swizzle. B (G, contiguous along k): lane = k.
-  Stage<NT> reg;
-  auto load = [&](int kb) {
+  auto load = [&](int kb, Regs& reg) {
     const int k0 = kb * kBK;
 #pragma unroll
-    for (int i = 0; i < Stage<NT>::kA / 4; ++i) {
+    for (int i = 0; i < Regs::kA / 4; ++i) {
       const int it = threadIdx.x + kThreads * i;
-      const int row = it % kM, c = it / kM;
+      const int row = it % kRows, c = it / kRows;
       const int64_t gr = r0 + row;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -287,16 +318,16 @@ tc_update_kernel(const double* __restrict__ A, int64_t lda, const double* __rest
     }
     const int gk = k0 + lane;
 #pragma unroll
-    for (int i = 0; i < Stage<NT>::kB; ++i) {
-      const int gc = c0 + warp + 8 * i;
+    for (int i = 0; i < Regs::kB; ++i) {
+      const int gc = c0 + warp + kWarps * i;
       reg.b[i] = (gk < m && gc < p) ? ld_hi(G + gk + (int64_t)gc * ldg) : 0u;
     }
   };
-  auto store = [&](uint8_t* a_tile, uint8_t* b_tile) {
+  auto store = [&](uint8_t* a_tile, uint8_t* b_tile, const Regs& reg) {
 #pragma unroll
-    for (int i = 0; i < Stage<NT>::kA / 4; ++i) {
+    for (int i = 0; i < Regs::kA / 4; ++i) {
       const int it = threadIdx.x + kThreads * i;
-      const int row = it % kM, c = it / kM;
+      const int row = it % kRows, c = it / kRows;
       uint4 v;
       v.x = tf32_from_hi(reg.a[4 * i + 0]);
       v.y = tf32_from_hi(reg.a[4 * i + 1]);
@@ -305,31 +336,35 @@ tc_update_kernel(const double* __restrict__ A, int64_t lda, const double* __rest
       *reinterpret_cast<uint4*>(a_tile + tile_off(row, 4 * c)) = v;
     }
 #pragma unroll
-    for (int i = 0; i < Stage<NT>::kB; ++i)
-      *reinterpret_cast<uint32_t*>(b_tile + tile_off(warp + 8 * i, lane)) = tf32_from_hi(reg.b[i]);
+    for (int i = 0; i < Regs::kB; ++i)
+      *reinterpret_cast<uint32_t*>(b_tile + tile_off(warp + kWarps * i, lane)) = tf32_from_hi(reg.b[i]);
   };
-  const bool ok = tc_mainloop(nk, align_tiles(dyn), a_bytes, b_bytes, sm, tmem, idesc_tf32(kM, NT), load, store);
+  const bool ok = tc_mainloop<Regs, MT, NT>(nk, align_tiles(dyn), a_bytes, b_bytes, sm, tmem, idesc_tf32(kM, NT),
+                                            load, store);
   if (ok) {
-    const int q = warp & 3, h = warp >> 2;
-    const int64_t gr = r0 + 32 * q + lane;
+    const int q = warp & 3, h = warp >> 2;         // TMEM lane quadrant; 16-column chunks h, h + kWarps/4, ...
 #pragma unroll 1
-    for (int cc = h * (NT / 2); cc < (h + 1) * (NT / 2); cc += 16) {
-      float v[16];
-      if (nk > 0) tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)cc, v);
-      else
+    for (int half = 0; half < MT; ++half) {
+      const int64_t gr = r0 + half * kM + 32 * q + lane;
+#pragma unroll 1
+      for (int cc = 16 * h; cc < NT; cc += 16 * (kWarps / 4)) {
+        float v[16];
+        if (nk > 0) tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(half * NT + cc), v);
+        else
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = 0.f;
-      if (gr < n) {
-        double y[16];
+          for (int i = 0; i < 16; ++i) v[i] = 0.f;
+        if (gr < n) {
+          double y[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int gc = c0 + cc + i;
-          y[i] = (subtract && gc < p) ? Y[gr + (int64_t)gc * ldy] : 0.0;
-        }
+          for (int i = 0; i < 16; ++i) {
+            const int gc = c0 + cc + i;
+            y[i] = (subtract && gc < p) ? Y[gr + (int64_t)gc * ldy] : 0.0;
+          }
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int gc = c0 + cc + i;
-          if (gc < p) Y[gr + (int64_t)gc * ldy] = subtract ? (y[i] - widen(v[i])) : widen(v[i]);
+          for (int i = 0; i < 16; ++i) {
+            const int gc = c0 + cc + i;
+            if (gc < p) Y[gr + (int64_t)gc * ldy] = subtract ? (y[i] - widen(v[i])) : widen(v[i]);
+          }
         }
       }
     }
@@ -344,12 +379,12 @@ int pick_nt(int cols) {
   return 256;
 }
 
-size_t tc_smem_bytes(int NT) { return 2 * ((size_t)kM * kRowB + (size_t)NT * kRowB) + 1024; }
+size_t tc_smem_bytes(int NT, int MT) { return 2 * ((size_t)MT * kM * kRowB + (size_t)NT * kRowB) + 1024; }
 
-// Sets the dynamic shared memory of fn to at least `bytes`, padded so that no more CTAs than 512 / NT can be
+// Sets the dynamic shared memory of fn to at least `bytes`, padded so that no more CTAs than 512 / cols can be
 // resident on one SM: tcgen05.alloc waits for free TMEM columns, and the SM has 512.
-cudaError_t set_smem(const void* fn, size_t& bytes, int NT) {
-  const int max_ctas = 512 / NT;
+cudaError_t set_smem(const void* fn, size_t& bytes, int cols) {
+  const int max_ctas = 512 / cols;
   for (int tries = 0; tries < 8; ++tries) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
@@ -373,27 +408,49 @@ int sm_count() {
 }
 
 
-template <int NT>
+template <int NT, int MT>
 cudaError_t launch_gram(dim3 grid, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n, int ma,
-                        int mb, int tiles_n, int64_t rows, double* part, int* flag, cudaStream_t s) {
-  size_t smem = tc_smem_bytes(NT);
-  cudaError_t e = set_smem((const void*)tc_gram_kernel<NT>, smem, NT);
+                        int mb, int tiles_n, int64_t rows, float* part, int* flag, cudaStream_t s) {
+  size_t smem = tc_smem_bytes(NT, MT);
+  cudaError_t e = set_smem((const void*)tc_gram_kernel<NT, MT>, smem, NT * MT);
   if (e != cudaSuccess) return e;
-  tc_gram_kernel<NT><<<grid, kThreads, smem, s>>>(A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag);
+  tc_gram_kernel<NT, MT><<<grid, kThreads, smem, s>>>(A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag);
   count_launch();
   return cudaGetLastError();
 }
 
-template <int NT>
+template <int MT>
+cudaError_t launch_gram_nt(int NT, dim3 grid, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n,
+                           int ma, int mb, int tiles_n, int64_t rows, float* part, int* flag, cudaStream_t s) {
+  switch (NT) {
+    case 32: return launch_gram<32, MT>(grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag, s);
+    case 64: return launch_gram<64, MT>(grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag, s);
+    case 128: return launch_gram<128, MT>(grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag, s);
+    default: return launch_gram<256, MT>(grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag, s);
+  }
+}
+
+template <int NT, int MT>
 cudaError_t launch_update(const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p, double* Y,
                           int64_t ldy, bool subtract, int* flag, cudaStream_t s) {
-  size_t smem = tc_smem_bytes(NT);
-  cudaError_t e = set_smem((const void*)tc_update_kernel<NT>, smem, NT);
+  size_t smem = tc_smem_bytes(NT, MT);
+  cudaError_t e = set_smem((const void*)tc_update_kernel<NT, MT>, smem, NT * MT);
   if (e != cudaSuccess) return e;
-  tc_update_kernel<NT><<<dim3((unsigned)ceil_div(n, kM), (unsigned)ceil_div(p, NT)), kThreads, smem, s>>>(
-      A, lda, G, ldg, n, m, p, Y, ldy, subtract ? 1 : 0, flag);
+  tc_update_kernel<NT, MT><<<dim3((unsigned)ceil_div(n, (int64_t)kM * MT), (unsigned)ceil_div(p, NT)), kThreads, smem,
+                             s>>>(A, lda, G, ldg, n, m, p, Y, ldy, subtract ? 1 : 0, flag);
   count_launch();
   return cudaGetLastError();
+}
+
+template <int MT>
+cudaError_t launch_update_nt(int NT, const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p,
+                             double* Y, int64_t ldy, bool subtract, int* flag, cudaStream_t s) {
+  switch (NT) {
+    case 32: return launch_update<32, MT>(A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
+    case 64: return launch_update<64, MT>(A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
+    case 128: return launch_update<128, MT>(A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
+    default: return launch_update<256, MT>(A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
+  }
 }
 
 }  // namespace
@@ -403,38 +460,39 @@ cudaError_t tc_gram(const double* A, int64_t lda, const double* B, int64_t ldb, 
   if (ma <= 0 || mb <= 0) return cudaSuccess;
   if ((size_t)ma * mb > part_capacity) return cudaErrorInvalidValue;
   const int NT = pick_nt(mb);
-  const int tiles_m = (int)ceil_div(ma, kM), tiles_n = (int)ceil_div(mb, NT);
+  const int MT = ma > kM ? 2 : 1;                  // two accumulators share each converted B tile
+  const int tiles_m = (int)ceil_div(ma, kM * MT), tiles_n = (int)ceil_div(mb, NT);
   const int tiles = tiles_m * tiles_n;
-  // enough CTAs to pull from HBM, while the FP64 partials stay below ~1/4 of the input bytes
-  int64_t nsplit = ceil_div(2LL * sm_count(), tiles);
-  const int64_t cap_traffic = (n * (int64_t)(ma + mb)) / (4LL * ma * mb) + 1;
+  // one wave of CTAs, while the FP32 partials (written, then read by the reduce; mostly L2-resident) stay below
+  // half of the input bytes
+  int64_t nsplit = ceil_div((int64_t)sm_count(), tiles);
+  const int64_t cap_traffic = (n * (int64_t)(ma + mb)) / (2LL * ma * mb) + 1;
   const int64_t cap_rows = ceil_div(n, 4 * kBK);
-  const int64_t cap_mem = (int64_t)(part_capacity / ((size_t)ma * mb));
+  const int64_t cap_mem = (int64_t)(2 * part_capacity / ((size_t)ma * mb));   // FP32 partials in FP64 space
   nsplit = std::min(nsplit, std::min(cap_traffic, std::min(cap_rows, cap_mem)));
   if (nsplit < 1) nsplit = 1;
   const int64_t rows = ceil_div(ceil_div(n, nsplit), kBK) * kBK;
   const int nsp = (int)ceil_div(n, rows);
   const dim3 grid(tiles, nsp);
-  cudaError_t e;
-  switch (NT) {
-    case 32: e = launch_gram<32>(grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag, s); break;
-    case 64: e = launch_gram<64>(grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag, s); break;
-    case 128: e = launch_gram<128>(grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag, s); break;
-    default: e = launch_gram<256>(grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag, s); break;
-  }
+  float* fpart = reinterpret_cast<float*>(part);     // FP32 partials in the FP64 partial buffer (half its bytes)
+  cudaError_t e = MT == 2 ? launch_gram_nt<2>(NT, grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, fpart, flag, s)
+                          : launch_gram_nt<1>(NT, grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, fpart, flag, s);
   if (e != cudaSuccess) return e;
-  return gram_reduce_partials(part, nsp, ma, mb, C, ldc, symmetric, s);
+  const int64_t blocks = ceil_div((int64_t)ma * mb, 256);
+  tc_reduce_kernel<<<(unsigned)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(fpart, nsp, ma, mb, C, ldc,
+                                                                            symmetric ? 1 : 0);
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t tc_update(const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p, double* Y,
                       int64_t ldy, bool subtract, int* flag, cudaStream_t s) {
   if (p <= 0 || n <= 0) return cudaSuccess;
-  switch (pick_nt(p)) {
-    case 32: return launch_update<32>(A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
-    case 64: return launch_update<64>(A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
-    case 128: return launch_update<128>(A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
-    default: return launch_update<256>(A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
-  }
+  const int NT = pick_nt(p);
+  // 256-row tiles (two accumulators sharing each converted G tile) unless that leaves more than half the SMs idle
+  const bool two = 2 * ceil_div(n, (int64_t)2 * kM) * ceil_div(p, NT) >= sm_count();
+  return two ? launch_update_nt<2>(NT, A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s)
+             : launch_update_nt<1>(NT, A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
 }
 
 }  // namespace ppcg

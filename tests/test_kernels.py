@@ -288,7 +288,8 @@ U_TF32 = 2.0 ** -11          # unit roundoff of TF32 (10 explicit mantissa bits,
 
 
 @pytest.mark.parametrize("N,ma,mb,sym", [(5, 37, 61, False), (10, 70, 130, False), (16, 256, 256, False),
-                                         (16, 130, 130, True), (16, 200, 33, False), (10, 1, 1, False)])
+                                         (16, 130, 130, True), (16, 200, 33, False), (10, 1, 1, False),
+                                         (30, 300, 260, False), (32, 256, 256, True)])
 def test_gram_tensor_core_tf32(N, ma, mb, sym):
     n = N ** 3
     rng = _rng(ma * 1000 + mb + 7)
@@ -309,7 +310,8 @@ def test_gram_tensor_core_tf32(N, ma, mb, sym):
         np.testing.assert_array_equal(C, C.T)
 
 
-@pytest.mark.parametrize("N,mx,my", [(11, 40, 25), (16, 256, 256), (16, 130, 70)])
+# n >= 19456 (N = 30, 32) takes the 256-row update tiles, smaller n the 128-row ones
+@pytest.mark.parametrize("N,mx,my", [(11, 40, 25), (16, 256, 256), (16, 130, 70), (32, 256, 256), (30, 130, 300)])
 def test_project_tensor_core_tf32(N, mx, my):
     n = N ** 3
     rng = _rng(mx + my)
