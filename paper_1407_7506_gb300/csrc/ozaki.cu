@@ -351,7 +351,7 @@ oz_gram_kernel(const double* __restrict__ A, int64_t lda, const double* __restri
         const int gj = n0 + cj;
         if (gj >= mb) continue;
         const int Ej = sm.Eb[cj];
-        const double v = (Ei == kNoExp || Ej == kNoExp) ? 0.0 : ((double)hi[i] + (double)lo[i]) * pow2(Ei + Ej - 10);
+        const double v = (Ei == kNoExp || Ej == kNoExp) ? 0.0 : (widen(hi[i]) + widen(lo[i])) * pow2(Ei + Ej - 10);
         out[gi + (int64_t)gj * ma] = v;
       }
     }
@@ -477,7 +477,7 @@ oz_update_kernel(const double* __restrict__ A, int64_t lda, const double* __rest
         const int gc = c0 + cj;
         if (gc >= p) continue;
         const int Ej = sm.Eb[cj];
-        const double v = (Ei == kNoExp || Ej == kNoExp) ? 0.0 : ((double)hi[i] + (double)lo[i]) * pow2(Ei + Ej - 10);
+        const double v = (Ei == kNoExp || Ej == kNoExp) ? 0.0 : (widen(hi[i]) + widen(lo[i])) * pow2(Ei + Ej - 10);
         Y[gr + (int64_t)gc * ldy] = mode == (int)Epi::Store ? v : yv[i] - v;
       }
     }
@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(kThreads, 1) oz_img_kernel(ImgArgs a) {
         if (gj >= a.mb) continue;
         const int Ej = sm.Eb[cj];
         const double v = (nst == 0 || Ei == kNoExp || Ej == kNoExp) ? 0.0
-                                                                    : ((double)hi[i] + (double)lo[i]) * pow2(Ei + Ej - 10);
+                                                                    : (widen(hi[i]) + widen(lo[i])) * pow2(Ei + Ej - 10);
         row[(int64_t)gj * ld] = (UPD && a.mode != (int)Epi::Store) ? yv[i] - v : v;
       }
     }

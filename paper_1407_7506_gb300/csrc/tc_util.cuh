@@ -12,9 +12,16 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// byte offset of element (row, k) in a K-major no-swizzle tile
-
-// instruction descriptor of tcgen05.mma .kind::tf32: D = F32, A = B = TF32, both K-major, N >> 3, M >> 4
+// exact FP32 -> FP64 widening by integer field moves (FP32 subnormals, far below any accumulated value here, become
+// zero; infinities and NaNs stay so): FP32 -> FP64 conversion instructions run on GB300's narrow FP64 pipe
+__device__ __forceinline__ double widen(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const uint32_t e = (b >> 23) & 0xFFu;
+  const uint32_t eo = e == 0xFFu ? 0x7FFu : e + 896u;
+  const uint32_t hi = e == 0u ? (b & 0x80000000u) : ((b & 0x80000000u) | (eo << 20) | ((b & 0x7FFFFFu) >> 3));
+  const uint32_t lo = e == 0u ? 0u : (b << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
 
 __device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
@@ -76,7 +83,6 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar_addr) {
 }
 
 // 16 consecutive 32-bit TMEM columns of this thread's lane
-
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
   asm volatile(

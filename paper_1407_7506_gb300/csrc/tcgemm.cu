@@ -76,17 +76,6 @@ __device__ __forceinline__ uint32_t ld_hi(const double* p) {
   return __ldg(reinterpret_cast<const uint32_t*>(p) + 1);
 }
 
-// exact FP32 -> FP64 widening by integer field moves (FP32 subnormals, far below any accumulated value here, become
-// zero; infinities and NaNs stay so)
-__device__ __forceinline__ double widen(float v) {
-  const uint32_t b = __float_as_uint(v);
-  const uint32_t e = (b >> 23) & 0xFFu;
-  const uint32_t eo = e == 0xFFu ? 0x7FFu : e + 896u;
-  const uint32_t hi = e == 0u ? (b & 0x80000000u) : ((b & 0x80000000u) | (eo << 20) | ((b & 0x7FFFFFu) >> 3));
-  const uint32_t lo = e == 0u ? 0u : (b << 29);
-  return __hiloint2double((int)hi, (int)lo);
-}
-
 struct TcSmem {
   uint64_t mbar[2];
   uint32_t tmem_slot;

@@ -9,59 +9,49 @@ namespace {
 
 constexpr int kRows = 64;   // rows per tile; must match gemm_nn's row tile (norm_part layout)
 
-// R = HX - lam_c X; W = R / max(dg - sigma, delta); per-tile sums of R^2 per column.
-__global__ void __launch_bounds__(256)
-residual_diag_kernel(const double* __restrict__ X, const double* __restrict__ HX, int64_t ld, int64_t n, int m,
-                     const double* __restrict__ lam, const double* __restrict__ dg, double sigma, double delta,
-                     double* __restrict__ W, double* __restrict__ norm_part) {
-  const int r_loc = threadIdx.x % kRows;
-  const int c_loc = threadIdx.x / kRows;          // 4 columns per block
-  const int64_t r = (int64_t)blockIdx.x * kRows + r_loc;
-  const int c = blockIdx.y * 4 + c_loc;
-  double sq = 0.0;
-  if (r < n && c < m) {
-    const int64_t o = (int64_t)c * ld + r;
-    const double rr = HX[o] - lam[c] * X[o];
-    sq = rr * rr;
-    W[o] = rr / fmax(dg[r] - sigma, delta);
-  }
-  // reduce over the 64 rows of this column: two warps
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
-  __shared__ double red[8];
-  const int warp = threadIdx.x / 32;
-  if ((threadIdx.x & 31) == 0) red[warp] = sq;
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    const int cc = blockIdx.y * 4 + threadIdx.x;
-    if (cc < m) norm_part[(int64_t)blockIdx.x * m + cc] = red[2 * threadIdx.x] + red[2 * threadIdx.x + 1];
-  }
-}
+constexpr int kColsPerThread = 8;   // columns per thread: one reciprocal of the diagonal serves all of them
 
-// W holds R: norm_part per row tile gets the column sums of R^2, then W = T R in place
+// RESID: R = HX - lam_c X, else R = W (already AX - XM). Then W = T R with T = 1 / max(dg - sigma, delta), and the
+// per-tile column sums of R^2 go to norm_part. A block covers 64 rows x 32 columns; each thread forms the reciprocal
+// of its row once (FP64 division is a long instruction sequence on GB300's narrow FP64 pipe) and applies it to 8
+// columns.
+template <bool RESID>
 __global__ void __launch_bounds__(256)
-precond_norms_kernel(double* __restrict__ W, int64_t ld, int64_t n, int m, const double* __restrict__ dg,
-                     double sigma, double delta, double* __restrict__ norm_part) {
+precond_kernel(const double* __restrict__ X, const double* __restrict__ HX, double* W, int64_t ld, int64_t n, int m,
+               const double* __restrict__ lam, const double* __restrict__ dg, double sigma, double delta,
+               double* __restrict__ norm_part) {
   const int r_loc = threadIdx.x % kRows;
-  const int c_loc = threadIdx.x / kRows;
+  const int c_loc = threadIdx.x / kRows;          // 4 column lanes; columns c0 + c_loc + 4 j
   const int64_t r = (int64_t)blockIdx.x * kRows + r_loc;
-  const int c = blockIdx.y * 4 + c_loc;
-  double sq = 0.0;
-  if (r < n && c < m) {
-    const int64_t o = (int64_t)c * ld + r;
-    const double rr = W[o];
-    sq = rr * rr;
-    W[o] = rr / fmax(dg[r] - sigma, delta);
-  }
+  const int c0 = blockIdx.y * 4 * kColsPerThread;
+  const double tinv = r < n ? 1.0 / fmax(dg[r] - sigma, delta) : 0.0;
+  double sq[kColsPerThread];
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
-  __shared__ double red[8];
+  for (int j = 0; j < kColsPerThread; ++j) {
+    const int c = c0 + c_loc + 4 * j;
+    sq[j] = 0.0;
+    if (r < n && c < m) {
+      const int64_t o = (int64_t)c * ld + r;
+      const double rr = RESID ? HX[o] - lam[c] * X[o] : W[o];
+      sq[j] = rr * rr;
+      W[o] = rr * tinv;
+    }
+  }
+  // reduce each column over the 64 rows of the tile: warps 2 c_loc and 2 c_loc + 1
+  __shared__ double red[8][kColsPerThread];
   const int warp = threadIdx.x / 32;
-  if ((threadIdx.x & 31) == 0) red[warp] = sq;
+#pragma unroll
+  for (int j = 0; j < kColsPerThread; ++j) {
+    double v = sq[j];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) red[warp][j] = v;
+  }
   __syncthreads();
-  if (threadIdx.x < 4) {
-    const int cc = blockIdx.y * 4 + threadIdx.x;
-    if (cc < m) norm_part[(int64_t)blockIdx.x * m + cc] = red[2 * threadIdx.x] + red[2 * threadIdx.x + 1];
+  if (threadIdx.x < 4 * kColsPerThread) {
+    const int cl = threadIdx.x % 4, j = threadIdx.x / 4;
+    const int c = c0 + cl + 4 * j;
+    if (c < m) norm_part[(int64_t)blockIdx.x * m + c] = red[2 * cl][j] + red[2 * cl + 1][j];
   }
 }
 
@@ -293,16 +283,17 @@ cudaError_t add_diag(double* Z, int m, double b, cudaStream_t s) {
 cudaError_t residual_diag(const double* X, const double* HX, int64_t ld, int64_t n, int m, const double* lam,
                           const ResidualArgs& ra, double* W, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
-  dim3 grid((unsigned)norm_row_tiles(n), (unsigned)ceil_div(m, 4));
-  residual_diag_kernel<<<grid, 256, 0, s>>>(X, HX, ld, n, m, lam, ra.dg, ra.sigma, ra.delta, W, ra.norm_part);
+  dim3 grid((unsigned)norm_row_tiles(n), (unsigned)ceil_div(m, 4 * kColsPerThread));
+  precond_kernel<true><<<grid, 256, 0, s>>>(X, HX, W, ld, n, m, lam, ra.dg, ra.sigma, ra.delta, ra.norm_part);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t precond_norms(double* W, int64_t ld, int64_t n, int m, const ResidualArgs& ra, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
-  dim3 grid((unsigned)norm_row_tiles(n), (unsigned)ceil_div(m, 4));
-  precond_norms_kernel<<<grid, 256, 0, s>>>(W, ld, n, m, ra.dg, ra.sigma, ra.delta, ra.norm_part);
+  dim3 grid((unsigned)norm_row_tiles(n), (unsigned)ceil_div(m, 4 * kColsPerThread));
+  precond_kernel<false><<<grid, 256, 0, s>>>(nullptr, nullptr, W, ld, n, m, nullptr, ra.dg, ra.sigma, ra.delta,
+                                             ra.norm_part);
   count_launch();
   return cudaGetLastError();
 }
