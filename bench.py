@@ -297,7 +297,7 @@ def main():
                 "phase_ms": {k_: round(v_, 2) for k_, v_ in pst["t_phase_ms"].items()},
                 "jacobi_sweeps_max": pst["jacobi_sweeps_max"],
                 "counts": {k_: stats[-1][k_] for k_ in ("n_rr", "n_drop_p", "n_cholqr_fallback", "n_polar",
-                                                         "n_orth_skip")}}
+                                                         "n_orth_skip", "n_eig_diagonal", "n_eig_refined")}}
 
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     clk = ClockSampler(local)

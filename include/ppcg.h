@@ -103,6 +103,8 @@ typedef struct {
   double max_res;             /* max_i ||A x_i - lambda_i x_i|| over the k returned pairs */
   int32_t n_orth_skip;        /* plain steps whose orthonormalisation was skipped (options.orth_skip_tol) */
   int32_t n_polar;            /* plain steps orthonormalised by the polar series (options.orth = 1) */
+  int32_t n_eig_diagonal;     /* Rayleigh-Ritz eigensolves whose matrix was already diagonal (no rotation needed) */
+  int32_t n_eig_refined;      /* Rayleigh-Ritz eigensolves finished by eigenvector refinement instead of Jacobi */
 } ppcg_stats;
 
 typedef struct ppcg_ctx* ppcg_handle;

@@ -55,6 +55,8 @@ struct ppcg_ctx {
   size_t evused = 0;
   double t_ms[8] = {};
   int last_sweeps = 0;
+  int eig_path = 0;           // route of the last dense_eigh: 0 Jacobi, 1 diagonal, 2 refined
+  int eig_count[3] = {0, 0, 0};   // dense_eigh calls of the current solve per route
   bool mixed = false;      // PPCG_MIXED_TF32: projections and the first CholQR Gram on tcgen05
   bool ozaki = false;      // FP64 n x k GEMMs emulated on the BF16 tensor cores (error-free splitting)
   int* ozexps = nullptr;   // exponent workspace of the emulated GEMMs
@@ -336,9 +338,15 @@ ppcg_status cholqr2(ppcg_ctx* c, double* X, int64_t ldx, double* Xs, int64_t ldx
   return PPCG_OK;
 }
 
+// Mm must not alias c->G (the symmetrisation scratch) or Cm
 ppcg_status dense_eigh(ppcg_ctx* c, const double* Mm, int m, double* lam, double* Cm) {
   CK(cudaMemsetAsync(c->iflag, 0, sizeof(int), c->stream));
-  CK(jacobi_eigh(Mm, m, lam, Cm, c->jacws, c->iflag, c->bar, c->jinfo, c->stream));
+  CK(cudaMemsetAsync(c->jinfo, 0, 2 * sizeof(int), c->stream));
+  int path = 0;
+  CK(dense_eigh_auto(Mm, m, lam, Cm, c->jacws, c->G, c->gpart, c->gpart_cap, c->iflag, c->bar, c->jinfo, &path,
+                     c->stream));
+  c->eig_path = path;
+  if (path >= 0 && path < 3) c->eig_count[path]++;
   return PPCG_OK;
 }
 
@@ -698,6 +706,7 @@ ppcg_status ppcg_solve(ppcg_handle c, const double* X0, double tol, double* lamb
   ppcg_stats local{};
   ppcg_stats* S = stats ? stats : &local;
   std::memset(S, 0, sizeof(*S));
+  c->eig_count[0] = c->eig_count[1] = c->eig_count[2] = 0;
   std::memset(c->t_ms, 0, sizeof(c->t_ms));
   c->evused = 0;
   const long long launches0 = launch_count();
@@ -836,6 +845,8 @@ ppcg_status ppcg_solve(ppcg_handle c, const double* X0, double tol, double* lamb
   S->converged = st.done ? 1 : 0;
   S->max_res = mx;
   S->kernel_launches = launch_count() - launches0;
+  S->n_eig_diagonal = c->eig_count[1];
+  S->n_eig_refined = c->eig_count[2];
   for (int i = 0; i < 8; ++i) S->t_phase_ms[i] = c->t_ms[i];
   return st.done ? PPCG_OK : PPCG_ERR_NOT_CONVERGED;
 }

@@ -465,6 +465,183 @@ __global__ void jacobi_gather_kernel(JacBuf b, int m, int mp, const int* info, c
   }
 }
 
+// ------------------------------------------------------------------------------- nearly diagonal matrices
+// Msym = M with its lower triangle taken from the upper one (the eigensolvers read the upper triangle)
+__global__ void symmetrize_kernel(const double* __restrict__ M, int m, double* __restrict__ Msym) {
+  const int64_t cnt = (int64_t)m * m;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    Msym[e] = i <= j ? M[e] : M[j + (int64_t)i * m];
+  }
+}
+
+// ||M||_F and max_{i != j} |M_ij| (one CTA: a fixed summation order, so repeated calls agree bit for bit)
+__global__ void eig_stats_kernel(const double* __restrict__ M, int m, double* out) {
+  double s = 0.0, mx = 0.0;
+  const int64_t cnt = (int64_t)m * m;
+  for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const double v = M[e];
+    s += v * v;
+    if (e % m != e / m) mx = fmax(mx, fabs(v));
+  }
+  __shared__ double rs[1024], rm[1024];
+  rs[threadIdx.x] = s;
+  rm[threadIdx.x] = mx;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) {
+      rs[threadIdx.x] += rs[threadIdx.x + off];
+      rm[threadIdx.x] = fmax(rm[threadIdx.x], rm[threadIdx.x + off]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = sqrt(rs[0]);
+    out[1] = rm[0];
+  }
+}
+
+// Refinement step, first half (Ogita and Aishima 2018, symmetric eigenvalue refinement): with R = I - Z^T Z
+// (G = Z^T Z; G = null means Z = I, R = 0) and S = Z^T M Z, lam_i = S_ii / (1 - R_ii) and the cluster radius
+// delta = 2 (||S - diag(lam)|| + ||M|| ||R||), Frobenius norms standing in for 2-norms (a larger delta only
+// treats more pairs as clustered). out: [0] delta, [1] max |E_ij| (as bits, set by the second half), [2] cluster
+// flag. One CTA.
+__global__ void refine_lam_kernel(const double* __restrict__ S, const double* __restrict__ G, int m, double nM,
+                                  double* lam, double* out) {
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double sii = S[i + (int64_t)i * m];
+    lam[i] = G ? sii / G[i + (int64_t)i * m] : sii;
+  }
+  __syncthreads();
+  double a = 0.0, b = 0.0;
+  const int64_t cnt = (int64_t)m * m;
+  for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    const double d = S[e] - (i == j ? lam[i] : 0.0);
+    a += d * d;
+    if (G) {
+      const double r = (i == j ? 1.0 : 0.0) - G[e];
+      b += r * r;
+    }
+  }
+  __shared__ double ra[1024], rb[1024];
+  ra[threadIdx.x] = a;
+  rb[threadIdx.x] = b;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) {
+      ra[threadIdx.x] += ra[threadIdx.x + off];
+      rb[threadIdx.x] += rb[threadIdx.x + off];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = 2.0 * (sqrt(ra[0]) + nM * sqrt(rb[0]));
+    out[1] = 0.0;
+    out[2] = 0.0;
+  }
+}
+
+// Second half: E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i) where |lam_j - lam_i| > delta, else R_ij / 2 (and a
+// pair coupled above thr there is flagged: the refinement cannot separate it); E_ii = R_ii / 2. The largest
+// |E_ij|, i != j, is merged by an atomic maximum on the bit pattern (order-independent).
+__global__ void refine_coef_kernel(const double* __restrict__ S, const double* __restrict__ G, int m,
+                                   const double* __restrict__ lam, double* stat, double thr, double* __restrict__ E) {
+  const double delta = stat[0];
+  double emax = 0.0;
+  bool clustered = false;
+  const int64_t cnt = (int64_t)m * m;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    const double r = G ? (i == j ? 1.0 : 0.0) - G[e] : 0.0;
+    double v;
+    if (i == j) {
+      v = 0.5 * r;
+    } else {
+      const double dl = lam[j] - lam[i];
+      if (fabs(dl) > delta) {
+        v = (S[e] + lam[j] * r) / dl;
+      } else {
+        v = 0.5 * r;
+        if (fabs(S[e]) > thr) clustered = true;
+      }
+      emax = fmax(emax, fabs(v));
+    }
+    E[e] = v;
+  }
+  if (!(emax == emax)) emax = CUDART_INF;    // a NaN coefficient rejects the refinement
+  for (int off = 16; off > 0; off >>= 1) {
+    emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+    clustered = __any_sync(0xffffffffu, clustered);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(reinterpret_cast<unsigned long long*>(stat + 1), (unsigned long long)__double_as_longlong(emax));
+    if (clustered) stat[2] = 1.0;
+  }
+}
+
+// Z = I + E (first step, from Z = I)
+__global__ void identity_plus_kernel(const double* __restrict__ E, int m, double* __restrict__ Z) {
+  const int64_t cnt = (int64_t)m * m;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x)
+    Z[e] = E[e] + ((e % m == e / m) ? 1.0 : 0.0);
+}
+
+__global__ void add_kernel(const double* __restrict__ T, int64_t cnt, double* __restrict__ Z) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x)
+    Z[e] += T[e];
+}
+
+// Rayleigh quotients lam_i = z_i^T (M z_i) / z_i^T z_i of the accepted vectors (T = M Z); one warp per column
+__global__ void rayleigh_quotient_kernel(const double* __restrict__ Z, const double* __restrict__ T, int m,
+                                         double* __restrict__ lam) {
+  const int col = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (col >= m) return;
+  double num = 0.0, den = 0.0;
+  for (int r = lane; r < m; r += 32) {
+    const double z = Z[r + (int64_t)col * m];
+    num += z * T[r + (int64_t)col * m];
+    den += z * z;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    num += __shfl_xor_sync(0xffffffffu, num, off);
+    den += __shfl_xor_sync(0xffffffffu, den, off);
+  }
+  if (lane == 0) lam[col] = num / den;
+}
+
+// lambda ascending by the strict total order (value, index), NaN as +inf; perm[rank] = index
+__global__ void rank_sort_kernel(const double* __restrict__ v, int64_t stride, int m, double* lambda, int* perm) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const double li = v[(int64_t)i * stride];
+    const double ki = isnan(li) ? CUDART_INF : li;
+    int rank = 0;
+    for (int l = 0; l < m; ++l) {
+      const double ll = v[(int64_t)l * stride];
+      const double kl = isnan(ll) ? CUDART_INF : ll;
+      rank += (kl < ki || (kl == ki && l < i)) ? 1 : 0;
+    }
+    lambda[rank] = li;
+    perm[rank] = i;
+  }
+}
+
+// C[:, r] = Z[:, perm[r]] (Z = null: the identity)
+__global__ void gather_perm_kernel(const double* __restrict__ Z, int m, const int* __restrict__ perm, double* C) {
+  const int64_t cnt = (int64_t)m * m;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % m), c = (int)(e / m);
+    const int pc = perm[c];
+    C[e] = Z ? Z[r + (int64_t)pc * m] : (r == pc ? 1.0 : 0.0);
+  }
+}
+
+inline unsigned grid_for(int64_t cnt) {
+  const int64_t b = ceil_div(cnt, 256);
+  return (unsigned)(b < 1 ? 1 : (b < 4096 ? b : 4096));
+}
+
 struct CoopLimit {
   int chol = 0, jac = 0;
 };
@@ -596,6 +773,91 @@ cudaError_t jacobi_eigh(const double* M, int m, double* lambda, double* C, doubl
                          0, s>>>(jb, m, mp, info, perm, C);
   count_launch();
   return cudaGetLastError();
+}
+
+// Eigen-decomposition of the Rayleigh-Ritz matrix M, cheapest route first. The matrix of a Rayleigh-Ritz step late
+// in a solve is nearly diagonal in the basis of the previous Ritz vectors, and then the parallel Jacobi method still
+// pays its full rounds of grid barriers. (1) If no off-diagonal entry exceeds kJacobiTol ||M||_F (the Jacobi stop
+// test), the eigenpairs are the sorted diagonal and unit vectors. (2) If none exceeds kRefineTau ||M||_F, the
+// eigenvectors are refined from the identity by the iteration of Ogita and Aishima (2018): each step is a few
+// m x m FP64 products, and the error roughly squares. A step whose largest coefficient |E_ij| is at most
+// kRefineAccept, with no pair left clustered above the threshold, is accepted: the remaining error of Z is of order
+// kRefineAccept^2, and the eigenvalues are the Rayleigh quotients of the final vectors. (3) Otherwise, or when
+// kRefineSteps steps do not get there, parallel Jacobi on M. path_out: 0 Jacobi, 1 diagonal, 2 refined.
+// msym: m x m scratch (not aliasing M or C) for the symmetrised M.
+cudaError_t dense_eigh_auto(const double* Min, int m, double* lambda, double* C, double* ws, double* msym,
+                            double* part, size_t part_cap, int* flag, unsigned* bar, int* sweeps_out_dev,
+                            int* path_out, cudaStream_t s) {
+  *path_out = 0;
+  if (m <= 0) return cudaSuccess;
+  const int mp = pad_jac(m);
+  const size_t sq = (size_t)mp * mp;
+  double* Z = ws;
+  double* E = ws + sq;
+  double* T = ws + 2 * sq;
+  double* S = ws + 3 * sq;
+  double* lamw = ws + 4 * sq;                 // the Jacobi diagonal/pair arrays (4 mp doubles)
+  double* stat = lamw + 4 * (size_t)mp;       // the Jacobi norm slot (8 doubles)
+  int* perm = reinterpret_cast<int*>(stat + 8) + kJacobiMaxSweeps + 8;
+  double* G = C;                              // Z^T Z lives in the output until the final gather
+  const double* M = msym;
+  symmetrize_kernel<<<grid_for((int64_t)m * m), 256, 0, s>>>(Min, m, msym);
+  count_launch();
+  cudaError_t e;
+  eig_stats_kernel<<<1, 1024, 0, s>>>(M, m, stat);
+  count_launch();
+  double h[3] = {0.0, 0.0, 0.0};
+  if ((e = cudaMemcpyAsync(h, stat, 2 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  const double nM = h[0], off = h[1], thr = kJacobiTol * nM;
+  if (std::isfinite(nM) && off <= thr) {
+    rank_sort_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(M, (int64_t)m + 1, m, lambda, perm);
+    count_launch();
+    gather_perm_kernel<<<grid_for((int64_t)m * m), 256, 0, s>>>(nullptr, m, perm, C);
+    count_launch();
+    *path_out = 1;
+    return cudaGetLastError();
+  }
+  if (std::isfinite(nM) && off <= kRefineTau * nM) {
+    const int64_t cnt = (int64_t)m * m;
+    for (int t = 0; t < kRefineSteps; ++t) {
+      const double* St = M;
+      const double* Gt = nullptr;
+      if (t > 0) {
+        if ((e = small_gemm(true, Z, m, Z, m, m, m, m, G, m, part, part_cap, s)) != cudaSuccess) return e;
+        if ((e = small_gemm(false, M, m, Z, m, m, m, m, T, m, part, part_cap, s)) != cudaSuccess) return e;
+        if ((e = small_gemm(true, Z, m, T, m, m, m, m, S, m, part, part_cap, s)) != cudaSuccess) return e;
+        St = S;
+        Gt = G;
+      }
+      refine_lam_kernel<<<1, 1024, 0, s>>>(St, Gt, m, nM, lamw, stat);
+      count_launch();
+      refine_coef_kernel<<<grid_for(cnt), 256, 0, s>>>(St, Gt, m, lamw, stat, thr, E);
+      count_launch();
+      if (t == 0) {
+        identity_plus_kernel<<<grid_for(cnt), 256, 0, s>>>(E, m, Z);
+        count_launch();
+      } else {
+        if ((e = small_gemm(false, Z, m, E, m, m, m, m, T, m, part, part_cap, s)) != cudaSuccess) return e;
+        add_kernel<<<grid_for(cnt), 256, 0, s>>>(T, cnt, Z);
+        count_launch();
+      }
+      if ((e = cudaMemcpyAsync(h, stat, 3 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+      if (h[1] <= kRefineAccept && h[2] == 0.0) {
+        if ((e = small_gemm(false, M, m, Z, m, m, m, m, T, m, part, part_cap, s)) != cudaSuccess) return e;
+        rayleigh_quotient_kernel<<<(unsigned)ceil_div(m, 8), 256, 0, s>>>(Z, T, m, lamw);
+        count_launch();
+        rank_sort_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(lamw, 1, m, lambda, perm);
+        count_launch();
+        gather_perm_kernel<<<grid_for(cnt), 256, 0, s>>>(Z, m, perm, C);
+        count_launch();
+        *path_out = 2;
+        return cudaGetLastError();
+      }
+    }
+  }
+  return jacobi_eigh(Min, m, lambda, C, ws, flag, bar, sweeps_out_dev, s);
 }
 
 }  // namespace ppcg

@@ -16,6 +16,9 @@ constexpr double kJacobiTol = 1e-14;    // k x k Jacobi: rotate while |a_pq| > k
                                         // left below that adds < ~1e-12 to a Ritz residual (tol is 1e-8)
 constexpr double kJacobiTolSmall = 1e-16;  // sub-block warp Jacobi
 constexpr int kJacobiMaxSweeps = 60;
+constexpr double kRefineTau = 1e-6;      // try eigenvector refinement when max |M_ij| (i != j) <= kRefineTau ||M||_F
+constexpr int kRefineSteps = 4;          // refinement steps before falling back to Jacobi
+constexpr double kRefineAccept = 1e-8;   // accept a refinement step whose largest |E_ij| (i != j) is at most this
 constexpr int kPolarMaxTerms = 8;        // most series terms of the polar orthonormalisation
 constexpr int kMaxSbsize = 16;          // 3q <= 48 fits the warp-level sub-block solver
 
@@ -146,6 +149,12 @@ size_t jacobi_ws_elems(int m);
 // lambda ascending (m), C (m x m) eigenvectors of symmetric M (m x m, upper read).
 cudaError_t jacobi_eigh(const double* M, int m, double* lambda, double* C, double* ws, int* flag, unsigned* bar,
                         int* sweeps_out_dev, cudaStream_t s);
+// The same decomposition, cheapest route first: diagonal M, eigenvector refinement of a nearly diagonal M, else
+// jacobi_eigh. ws: jacobi_ws_elems(m); msym: m x m scratch; part: small_gemm partials (>= m * m). Synchronises
+// the stream. path_out: 0 Jacobi, 1 diagonal, 2 refined.
+cudaError_t dense_eigh_auto(const double* M, int m, double* lambda, double* C, double* ws, double* msym,
+                            double* part, size_t part_cap, int* flag, unsigned* bar, int* sweeps_out_dev,
+                            int* path_out, cudaStream_t s);
 size_t barrier_words();
 
 }  // namespace ppcg

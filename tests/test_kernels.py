@@ -158,6 +158,50 @@ def test_dense_eigh_degenerate_cluster():
     assert np.linalg.norm(Pg - Pr, 2) < 1e-12
 
 
+def _eigh_dev(M, m, N=8):
+    with Handle(np.zeros(N ** 3), N, kt=max(m, 1), sbsize=1) as H:
+        Md = dev(M)
+        ld = torch.empty(m, dtype=torch.float64, device="cuda")
+        Cd = torch.empty((m, m), dtype=torch.float64, device="cuda")
+        pk.ppcg_dense_eigh(H.h, ptr(Md), m, ptr(ld), ptr(Cd))
+        return ld.cpu().numpy(), host(Cd)
+
+
+@pytest.mark.parametrize("m,eps", [(40, 1e-6), (256, 1e-9), (256, 1e-6), (200, 3e-5)])
+def test_dense_eigh_nearly_diagonal(m, eps):
+    # the Rayleigh-Ritz matrices of a converging solve: off-diagonal entries far below the gaps (refinement route)
+    rng = _rng(m + 11)
+    lam = rng.permutation(np.linspace(-3.0, 5.0, m))
+    B = rng.standard_normal((m, m))
+    M = np.diag(lam) + eps * (B + B.T)
+    got_l, C = _eigh_dev(M, m)
+    ref_l = np.linalg.eigvalsh(M)
+    nrm = np.linalg.norm(M)
+    np.testing.assert_allclose(got_l, ref_l, rtol=0, atol=1e-13 * nrm)
+    np.testing.assert_allclose(C.T @ C, np.eye(m), atol=1e-12)
+    np.testing.assert_allclose(M @ C, C * got_l, atol=1e-12 * nrm)
+
+
+def test_dense_eigh_diagonal_and_cluster():
+    m = 64
+    rng = _rng(5)
+    lam = rng.permutation(np.linspace(-1.0, 2.0, m))
+    # exactly diagonal, unsorted: the eigenvectors are unit vectors in ascending order of the diagonal
+    got_l, C = _eigh_dev(np.diag(lam), m)
+    np.testing.assert_array_equal(got_l, np.sort(lam))
+    np.testing.assert_array_equal(C, np.eye(m)[:, np.argsort(lam, kind="stable")])
+    # nearly diagonal with two entries 1e-13 apart coupled by 1e-9: refinement cannot separate the pair
+    lam2 = lam.copy()
+    lam2[7] = lam2[3] + 1e-13
+    M = np.diag(lam2)
+    M[3, 7] = M[7, 3] = 1e-9
+    M[10, 20] = M[20, 10] = 1e-7
+    got_l, C = _eigh_dev(M, m)
+    np.testing.assert_allclose(got_l, np.linalg.eigvalsh(M), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(C.T @ C, np.eye(m), atol=1e-13)
+    np.testing.assert_allclose(M @ C, C * got_l, atol=1e-14)
+
+
 # ------------------------------------------------------------------------------------- sub-blocks (a7, a8, a9)
 def _block_inputs(N, k, seed, with_p):
     n = N ** 3

@@ -207,6 +207,9 @@ def test_solve_config1_against_dense_golden():
     assert st["converged"] == 1, st
     assert np.all(_rel(lam, gold) <= LAM_TOL), np.max(_rel(lam, gold))
     _check_pairs(V, w.N, lam, X, w.tol)
+    # late Rayleigh-Ritz matrices are diagonal or nearly so: those eigensolves skip the Jacobi sweeps
+    assert st["n_eig_diagonal"] > 0 and st["n_eig_refined"] > 0, st
+    assert st["n_eig_diagonal"] + st["n_eig_refined"] < st["n_rr"], st
 
 
 def test_solve_config2_full_size():
