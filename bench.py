@@ -36,8 +36,11 @@ METRIC = "time-to-tol 1e-8 and PPCG iters/s, mixed vs FP64 form on 1 GB300; % ro
 # FP64 FMA pipe of GB300: 2 FMA lanes per SM per clock (measured: a DFMA stream reaches 1.195 TFLOP/s at 1.97 GHz)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12          # 1.2586, at the 2070 MHz maximum SM clock
 # dram bytes (read + write) per launch of the roofline kernel, from one ncu capture of this shape
-# (profiles/gram_tn_kernel_grid32_k256.md: 134.66 MB read + 9.42 MB written)
+# (134.66 MB read + 9.42 MB written)
 ROOFLINE_TRAFFIC_BYTES = 144.08e6
+# DRAM bytes (read + write) of one tc_gram_kernel<256,2> launch, 32768 x 256 x 256, from one ncu capture
+# (134.27 MB read + 3.62 MB written: the FP32 split-K partials stay mostly in L2)
+TF32_GRAM_TRAFFIC_BYTES = 137.89e6
 L2_BYTES = 129 * 2 ** 20
 
 
@@ -592,7 +595,8 @@ def roofline_tc(pk, solver, w, dev, stream):
     peak, kind = hbm_peak()
     ach = nbytes / dur / 1e9
     return {"kernel": f"tc_gram_kernel (tcgen05 TF32, + split-K reduce): X^T W, n={n}, {k}x{k}", "bound": "hbm",
-            "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+            "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": TF32_GRAM_TRAFFIC_BYTES if (n, k) == (32768, 256) else None,
             "algorithmic_bytes_per_launch": nbytes, "launch_ms": dur * 1e3, "tflops": 2.0 * n * k * k / dur / 1e12,
             "peak_note": f"{kind} HBM copy bandwidth"}
 
