@@ -39,8 +39,11 @@ PPCG_API ppcg_status ppcg_cholqr2(ppcg_handle h, double* X, int64_t ldx, int32_t
 
 /* Symmetric eigensolver of the Rayleigh-Ritz step (steps 23-24, Section 5.5): M is m x m (leading dimension m,
  * the upper triangle is read), lambda receives the m eigenvalues ascending and C (m x m) the orthonormal
- * eigenvectors as columns. Parallel cyclic Jacobi; synchronises the stream and returns PPCG_ERR_TIMEOUT if a
- * bounded device wait gave up. */
+ * eigenvectors as columns. M, lambda and C are device buffers owned by the caller; C must not overlap M.
+ * Route: if no off-diagonal entry exceeds 1e-14 ||M||_F, the sorted diagonal and unit vectors. If none exceeds
+ * 1e-6 ||M||_F, eigenvector refinement from the identity (Ogita and Aishima 2018), accepted once every correction
+ * is <= 1e-8, with Rayleigh-quotient eigenvalues. Otherwise, or if refinement does not settle within 4 steps,
+ * parallel cyclic Jacobi. Synchronises the stream; returns PPCG_ERR_TIMEOUT if a bounded device wait gave up. */
 PPCG_API ppcg_status ppcg_dense_eigh(ppcg_handle h, const double* M, int32_t m, double* lambda, double* C);
 
 /* Steps 11-13 (eq. projev on S_j = [X_j, W_j, P_j], Section 5.1): for each of the s = ceil(k_act/q) sub-blocks
