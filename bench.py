@@ -42,6 +42,8 @@ ROOFLINE_TRAFFIC_BYTES = 144.08e6
 # (134.27 MB read + 3.62 MB written: the FP32 split-K partials stay mostly in L2)
 TF32_GRAM_TRAFFIC_BYTES = 137.89e6
 L2_BYTES = 129 * 2 ** 20
+WORKLOADS = {"grid32_k256": wl.GRID32_K256, "grid16_k64": wl.GRID16_K64, "grid48_k1024": wl.GRID48_K1024,
+             "grid32_k128_bloch": wl.GRID32_K128_BLOCH}
 
 
 def _env_rank():
@@ -136,7 +138,7 @@ def cpu_oracle_sample(w, iters):
 
 def oracle_full_iters():
     """Iterations the oracle needed on the benchmark workload (stored by tests/golden/make_golden.py)."""
-    path = os.path.join(ROOT, "tests", "golden", "config2_oracle_eigs.txt")
+    path = os.path.join(ROOT, "tests", "golden", "grid32_k256_oracle_eigs.txt")
     if not os.path.exists(path):
         return None, None
     head = open(path).readline() + open(path).readlines()[1]
@@ -214,9 +216,9 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2",
-                    help="1 = 16^3 k=64, 2 = 32^3 k=256 (default), 4 = the 64-problem batch, "
-                         "5 = the complex Bloch recipe at 32^3 k=128")
+    ap.add_argument("--workload", default="grid32_k256", choices=list(WORKLOADS) + ["batch64"],
+                    help="grid32_k256 (default), grid16_k64, grid48_k1024 (mixed-form size), "
+                         "grid32_k128_bloch (the complex Bloch recipe), batch64 (64 uneven problems)")
     ap.add_argument("--maxiter", type=int, default=6000)
     ap.add_argument("--ref-iters", type=int, default=3, help="oracle iterations per reference-arm step")
     ap.add_argument("--cpu-iters", type=int, default=3, help="oracle iterations in the cpu_baseline sample")
@@ -228,13 +230,13 @@ def main():
     ap.add_argument("--batch-gemm", default="fma", choices=["fma", "ozaki"],
                     help="FP64 GEMMs of the batched workload: FP64 FMA pipe or Ozaki emulation on tcgen05")
     args = ap.parse_args()
-    if args.workload == "4":
+    if args.workload == "batch64":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no oracle arm: 64 CPU "
                               "solves do not fit a bounded sample"}), flush=True)
             return 0
         return run_batched(args)
-    w = wl.REDUCED[5] if args.workload == "5" else wl.CONFIGS[int(args.workload)]
+    w = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
 
@@ -257,7 +259,7 @@ def main():
     V, X0 = wl.make_inputs(w)
     V_d = torch.from_numpy(V).to(dev)
     X0_d = torch.from_numpy(np.ascontiguousarray(X0.T)).to(dev)         # (k, n) rows = columns of X0
-    _, gold = oracle_full_iters() if args.workload == "2" else (None, None)
+    _, gold = oracle_full_iters() if args.workload == "grid32_k256" else (None, None)
     cplx = w.dtype == "c128"
     sk = {"dtype": w.dtype, "theta": w.theta} if cplx else {}          # Solver arguments of the operator
 
@@ -334,7 +336,7 @@ def main():
     e2e = None if args.no_e2e else run_e2e(pk, w, V, X0, max(1, args.steps // 2), stream)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, args.cpu_iters, iters // max(1, args.steps), stored=args.workload == "2")
+        cpu = cpu_baseline(w, args.cpu_iters, iters // max(1, args.steps), stored=args.workload == "grid32_k256")
     if rank != 0:
         return 0
     line = {

@@ -54,7 +54,7 @@ def test_batch_equals_individual_solves_and_dense_eigh():
         assert np.max(r) <= 1e-8 * (1 + 1e-6)
 
 
-def test_config4_batch_of_64_problems():
+def test_batch_of_64_problems():
     ws = wl.batch()                                                 # 64 problems, N in 12..28, k in 32..256
     probs = _problems(ws)
     bs = pk.BatchSolver([p for p, _, _ in probs], maxiter=5000)

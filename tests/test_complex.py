@@ -129,8 +129,8 @@ def test_complex_energy_gradient_and_finite_differences():
         s.close()
 
 
-def test_config5_recipe_at_reduced_size():
-    # the config-5 operator (64 wells on a Bloch-twisted grid) scaled to 12^3, k = 24, sbsize = 4
+def test_bloch_wells_recipe_at_12cubed():
+    # the 64^3 Bloch recipe (64 wells on a Bloch-twisted grid) scaled to 12^3, k = 24, sbsize = 4
     w = wl.small("c5s", N=12, k=24, sbsize=4, potential="wells", n_wells=8, seed=1005, dtype="c128", theta=THETA)
     V, X0 = wl.make_inputs(w)
     lam, X, res, st = _solve(V, w.N, w.k, w.sbsize, X0, fp64_gemm="ozaki")

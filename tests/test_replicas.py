@@ -58,5 +58,5 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
     class A:
         warmup, steps, ref_iters = 1, 1, 1
-    assert bench.run_reference(A, wl.CONFIGS[1]) == 0
+    assert bench.run_reference(A, wl.GRID16_K64) == 0
     assert capsys.readouterr().out == ""

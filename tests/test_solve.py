@@ -130,10 +130,10 @@ def test_mixed_form_solve(N, k, q):
     assert np.all(_rel(lam, ev) <= LAM_TOL_MIXED), np.max(_rel(lam, ev))
 
 
-def test_mixed_form_config1_against_dense_golden():
-    w = wl.CONFIGS[1]
+def test_mixed_form_grid16_k64_against_dense_golden():
+    w = wl.GRID16_K64
     V, X0 = wl.make_inputs(w)
-    gold = np.loadtxt(os.path.join(GOLDEN, "config1_dense_eigs.txt"))[:w.k]
+    gold = np.loadtxt(os.path.join(GOLDEN, "grid16_k64_dense_eigs.txt"))[:w.k]
     lam, X, res, st = _gpu_solve(V, w.N, w.k, w.sbsize, w.rr_period, X0, tol=w.tol, maxiter=5000, precision="mixed")
     assert st["converged"] == 1, st
     assert np.all(_rel(lam, gold) <= LAM_TOL_MIXED), np.max(_rel(lam, gold))
@@ -141,11 +141,11 @@ def test_mixed_form_config1_against_dense_golden():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_fp64_emulation_solve_config1(precision):
+def test_fp64_emulation_solve_grid16_k64(precision):
     # every FP64 n x k GEMM on the tensor cores (error-free splitting): the FP64-form bars still hold
-    w = wl.CONFIGS[1]
+    w = wl.GRID16_K64
     V, X0 = wl.make_inputs(w)
-    gold = np.loadtxt(os.path.join(GOLDEN, "config1_dense_eigs.txt"))[:w.k]
+    gold = np.loadtxt(os.path.join(GOLDEN, "grid16_k64_dense_eigs.txt"))[:w.k]
     lam, X, res, st = _gpu_solve(V, w.N, w.k, w.sbsize, w.rr_period, X0, tol=w.tol, maxiter=5000,
                                  precision=precision, fp64_gemm="ozaki")
     assert st["converged"] == 1, st
@@ -178,10 +178,10 @@ def test_orth_variants_solve(orth, skip, precision, gemm):
     assert st["iters"] <= 2 * ref.iters + 50, (st["iters"], ref.iters)
 
 
-def test_polar_form_config1_against_dense_golden():
-    w = wl.CONFIGS[1]
+def test_polar_form_grid16_k64_against_dense_golden():
+    w = wl.GRID16_K64
     V, X0 = wl.make_inputs(w)
-    gold = np.loadtxt(os.path.join(GOLDEN, "config1_dense_eigs.txt"))
+    gold = np.loadtxt(os.path.join(GOLDEN, "grid16_k64_dense_eigs.txt"))
     lam, X, res, st = _gpu_solve(V, w.N, w.k, w.sbsize, w.rr_period, X0, orth="polar")
     assert st["status"] == "ok" and st["converged"] == 1 and st["n_polar"] > 0
     assert np.all(_rel(lam, gold[:w.k]) <= LAM_TOL)
@@ -198,11 +198,11 @@ def test_solve_k1():
     _check_pairs(V, N, lam, X, 1e-8)
 
 
-def test_solve_config1_against_dense_golden():
+def test_solve_grid16_k64_against_dense_golden():
     # 16^3 grid, k = 64, sbsize = 1, rr_period = 5, V ~ U[0, 1)
-    w = wl.CONFIGS[1]
+    w = wl.GRID16_K64
     V, X0 = wl.make_inputs(w)
-    gold = np.loadtxt(os.path.join(GOLDEN, "config1_dense_eigs.txt"))[:w.k]
+    gold = np.loadtxt(os.path.join(GOLDEN, "grid16_k64_dense_eigs.txt"))[:w.k]
     lam, X, res, st = _gpu_solve(V, w.N, w.k, w.sbsize, w.rr_period, X0, tol=w.tol, maxiter=5000)
     assert st["converged"] == 1, st
     assert np.all(_rel(lam, gold) <= LAM_TOL), np.max(_rel(lam, gold))
@@ -212,9 +212,9 @@ def test_solve_config1_against_dense_golden():
     assert st["n_eig_diagonal"] + st["n_eig_refined"] < st["n_rr"], st
 
 
-def test_solve_config2_full_size():
+def test_solve_grid32_k256_full_size():
     # 32^3 grid, k = 256, sbsize = 4, 8 Gaussian wells: the benchmarked workload
-    w = wl.CONFIGS[2]
+    w = wl.GRID32_K256
     V, X0 = wl.make_inputs(w)
     lam, X, res, st = _gpu_solve(V, w.N, w.k, w.sbsize, w.rr_period, X0, tol=w.tol, maxiter=5000)
     assert st["converged"] == 1, st
@@ -222,15 +222,15 @@ def test_solve_config2_full_size():
     cols = np.random.default_rng(0).choice(w.k, 24, replace=False)
     r = np.linalg.norm(oracle.apply_H(V, w.N, 1.0, X[:, cols]) - X[:, cols] * lam[cols], axis=0)
     assert np.max(r) <= w.tol * (1 + 1e-6)
-    path = os.path.join(GOLDEN, "config2_oracle_eigs.txt")
+    path = os.path.join(GOLDEN, "grid32_k256_oracle_eigs.txt")
     if os.path.exists(path):
         gold = np.loadtxt(path)[:, 0]
         assert np.all(_rel(lam, gold) <= LAM_TOL), np.max(_rel(lam, gold))
 
 
 @pytest.mark.slow
-def test_config3_size_mixed_form_against_separable_spectrum():
-    # the config-3 shape and form (48^3, k = 1024, sbsize = 8, TF32 projections, FP64-accurate GEMMs otherwise)
+def test_grid48_k1024_mixed_form_against_separable_spectrum():
+    # the 48^3, k = 1024 shape and form (sbsize = 8, TF32 projections, FP64-accurate GEMMs otherwise)
     # with a separable potential, whose spectrum is known exactly: sums of three 1-D spectra
     N, k, q = 48, 1024, 8
     w = wl.small("sep48", N=N, k=k, sbsize=q, potential="separable", seed=1003)

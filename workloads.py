@@ -8,7 +8,7 @@ stencil operator H = -Δ_h + diag(V) on an N x N x N periodic grid.
 Layout: a grid function is a flat array of n = N^3 doubles with linear index p = i + N*j + N^2*l
 (x fastest). A block of k vectors is an (n, k) array in Fortran (column-major) order.
 
-Recipes (seed = 1000 + config index, numpy default_rng; draw order: V, then X0):
+Recipes (numpy default_rng with one seed per workload, 1001-1005; draw order: V, then X0):
   uniform      V_p ~ U[0, 1)
   wells        V = sum over w of -d_w * exp(-|r - c_w|^2 / (2 s_w^2)) + U[0, noise), with
                d_w ~ U[2, 6], s_w ~ U[2, 4] grid points, c_w ~ U[0, N)^3 and the periodic
@@ -17,7 +17,7 @@ Recipes (seed = 1000 + config index, numpy default_rng; draw order: V, then X0):
   zero         V = 0                                                  (test-only recipe)
 X0 = standard_normal((n, k)) laid out column-major (real); complex X0 = real + 1j*imag from two draws.
 
-The batched workload (config 4) is a list of independent problems: from default_rng(1004) draw the 64 grid
+The batched workload is a list of independent problems: from default_rng(1004) draw the 64 grid
 sizes N_i ~ U{12..28} and then the 64 block sizes k_i ~ U{32..256}; problem i then draws V_i ~ U[0, 1) and its
 X0_i from default_rng(1004 * 1000 + i) (V first, then X0).
 """
@@ -49,28 +49,23 @@ class Workload:
         return self.N ** 3
 
 
-# The five workloads of the method's benchmark set (plain, FP64 on GPU, mixed, batched, complex).
-CONFIGS = {
-    1: Workload("grid16_k64_q1_uniform", N=16, k=64, sbsize=1, potential="uniform", seed=1001),
-    2: Workload("grid32_k256_q4_wells8", N=32, k=256, sbsize=4, potential="wells", n_wells=8, seed=1002),
-    3: Workload("grid48_k1024_q8_wells32", N=48, k=1024, sbsize=8, potential="wells", n_wells=32, seed=1003,
-                precision="mixed"),
-    5: Workload("grid64_k2048_q8_wells64_bloch", N=64, k=2048, sbsize=8, potential="wells", n_wells=64,
-                seed=1005, dtype="c128", theta=(0.3, 0.7, 1.1)),
-}
-
-
-# Configurations too large to converge within a benchmark run on one GPU, at the largest size that does: the
-# config-5 recipe (Bloch twist, Gaussian wells + noise, complex vectors) on a 32^3 grid with k = 128.
-REDUCED = {
-    5: Workload("grid32_k128_q4_wells8_bloch", N=32, k=128, sbsize=4, potential="wells", n_wells=8, seed=1005,
-                dtype="c128", theta=(0.3, 0.7, 1.1)),
-}
+# The workloads of the method's benchmark set: plain FP64 at two sizes, the mixed form at 48^3, and the complex
+# Bloch recipe (its full 64^3, k = 2048 size does not converge within a benchmark run on one GPU, so it is also
+# defined at the largest size that does: 32^3 with k = 128). The batched set is batch() below.
+GRID16_K64 = Workload("grid16_k64_q1_uniform", N=16, k=64, sbsize=1, potential="uniform", seed=1001)
+GRID32_K256 = Workload("grid32_k256_q4_wells8", N=32, k=256, sbsize=4, potential="wells", n_wells=8, seed=1002)
+GRID48_K1024 = Workload("grid48_k1024_q8_wells32", N=48, k=1024, sbsize=8, potential="wells", n_wells=32,
+                        seed=1003, precision="mixed")
+GRID64_K2048_BLOCH = Workload("grid64_k2048_q8_wells64_bloch", N=64, k=2048, sbsize=8, potential="wells",
+                              n_wells=64, seed=1005, dtype="c128", theta=(0.3, 0.7, 1.1))
+GRID32_K128_BLOCH = Workload("grid32_k128_q4_wells8_bloch", N=32, k=128, sbsize=4, potential="wells", n_wells=8,
+                             seed=1005, dtype="c128", theta=(0.3, 0.7, 1.1))
 
 
 def batch(count: int = 64, seed: int = 1004, n_range=(12, 28), k_range=(32, 256), sbsize: int = 4):
-    """The batched workload: `count` independent uniform-potential problems of uneven size (config 4 with the
-    defaults). Returns a list of Workloads; make_inputs(w) draws each problem's V and X0 from its own seed."""
+    """The batched workload: `count` independent uniform-potential problems of uneven size (64 problems, N in
+    12..28, k in 32..256 with the defaults). Returns a list of Workloads; make_inputs(w) draws each problem's V
+    and X0 from its own seed."""
     rng = np.random.default_rng(seed)
     Ns = rng.integers(n_range[0], n_range[1] + 1, size=count)
     ks = rng.integers(k_range[0], k_range[1] + 1, size=count)
