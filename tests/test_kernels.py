@@ -202,6 +202,23 @@ def test_dense_eigh_diagonal_and_cluster():
     np.testing.assert_allclose(M @ C, C * got_l, atol=1e-14)
 
 
+def test_dense_eigh_tiny_and_repeated_diagonal():
+    # m = 1 and m = 2 (diagonal, nearly diagonal, dense) and a diagonal with repeated values: equal eigenvalues
+    # keep their index order, so the eigenvectors are the unit vectors in a stable sort of the diagonal
+    got_l, C = _eigh_dev(np.array([[-2.5]]), 1)
+    np.testing.assert_array_equal(got_l, [-2.5])
+    np.testing.assert_array_equal(C, [[1.0]])
+    for M in (np.diag([3.0, -1.0]), np.array([[3.0, 1e-9], [1e-9, -1.0]]), np.array([[1.0, 2.0], [2.0, -3.0]])):
+        got_l, C = _eigh_dev(M, 2)
+        np.testing.assert_allclose(got_l, np.linalg.eigvalsh(M), rtol=0, atol=1e-14 * np.linalg.norm(M))
+        np.testing.assert_allclose(C.T @ C, np.eye(2), atol=1e-15)
+        np.testing.assert_allclose(M @ C, C * got_l, atol=1e-14 * np.linalg.norm(M))
+    d = np.array([2.0, 0.5, 2.0, -1.0, 0.5, 2.0, 0.0, -1.0])
+    got_l, C = _eigh_dev(np.diag(d), len(d))
+    np.testing.assert_array_equal(got_l, np.sort(d))
+    np.testing.assert_array_equal(C, np.eye(len(d))[:, np.argsort(d, kind="stable")])
+
+
 # ------------------------------------------------------------------------------------- sub-blocks (a7, a8, a9)
 def _block_inputs(N, k, seed, with_p):
     n = N ** 3
