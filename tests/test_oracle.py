@@ -6,6 +6,7 @@ of the periodic (and Bloch-twisted) 7-point Laplacian; separable potentials whos
 of Section 5.1; Theorem 2; Courant-Fischer bounds on Ritz values.
 """
 import itertools
+import os
 
 import numpy as np
 import pytest
@@ -504,3 +505,22 @@ def test_constant_potential_shift_moves_energy_by_k_c():
     E0 = np.sum(np.linalg.eigvalsh(oracle.assemble_H(V, N, 1.0))[:k])
     E1 = np.sum(np.linalg.eigvalsh(oracle.assemble_H(V + c, N, 1.0))[:k])
     np.testing.assert_allclose(E1 - E0, k * c, rtol=1e-12)
+
+
+@pytest.mark.skipif(not os.environ.get("PPCG_SLOW_PINS"), reason="about 5 minutes of CPU; set PPCG_SLOW_PINS=1")
+def test_stored_grid32_k256_values_match_sparse_lanczos():
+    # the stored oracle eigenvalues of the 32^3, 8-well operator against ARPACK (scipy eigsh, shift-invert) on the
+    # operator assembled as a sum of Kronecker products: a library eigensolver that shares nothing with the oracle
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    w = wl.GRID32_K256
+    V, _ = wl.make_inputs(w)
+    N = w.N
+    one = np.ones(N)
+    L1 = sp.diags([2 * one, -one[:-1], -one[:-1], [-1.0], [-1.0]], [0, 1, -1, N - 1, -(N - 1)], format="csr")
+    I = sp.identity(N, format="csr")
+    # linear index p = i + N j + N^2 l: the x axis is the fastest, i.e. the last Kronecker factor
+    H = (sp.kron(sp.kron(I, I), L1) + sp.kron(sp.kron(I, L1), I) + sp.kron(sp.kron(L1, I), I) + sp.diags(V)).tocsc()
+    ref = np.sort(spla.eigsh(H, k=w.k + 8, sigma=V.min() - 0.5, which="LM", return_eigenvectors=False, tol=1e-13))
+    gold = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "grid32_k256_oracle_eigs.txt"))[:, 0]
+    assert np.max(np.abs(gold - ref[:w.k]) / np.maximum(np.abs(ref[:w.k]), 1)) <= 1e-12
