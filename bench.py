@@ -205,8 +205,8 @@ FORM_TEXT = {
     "mixed": "TF32 tcgen05 projection GEMMs and first CholeskyQR Gram; everything else FP64",
     "fp64_ozaki": "FP64 with the n x k GEMMs emulated on BF16 tcgen05 (8 digit slices, Ozaki)",
     "mixed_ozaki": "mixed (TF32 projections) with the other FP64 n x k GEMMs emulated on BF16 tcgen05 (Ozaki)",
-    "fp64_ozaki_polar": "fp64_ozaki with the polar-series orthonormalisation of Section 5.4",
-    "mixed_ozaki_polar": "mixed_ozaki with the polar-series orthonormalisation of Section 5.4",
+    "fp64_ozaki_polar": "fp64_ozaki with the polar-series orthonormalisation of Section 5.5",
+    "mixed_ozaki_polar": "mixed_ozaki with the polar-series orthonormalisation of Section 5.5",
 }
 
 

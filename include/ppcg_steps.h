@@ -31,13 +31,13 @@ PPCG_API ppcg_status ppcg_gram(ppcg_handle h, const double* A, int64_t lda, cons
 PPCG_API ppcg_status ppcg_project(ppcg_handle h, const double* X, int64_t ldx, int32_t mx, double* Y, int64_t ldy,
                          int32_t my);
 
-/* Steps 18-19 (Section 5.4), applied twice (CholeskyQR2): X <- X R^{-1} with X^T X = R^T R, R upper triangular
+/* Steps 18-19 (Section 5.5), applied twice (CholeskyQR2): X <- X R^{-1} with X^T X = R^T R, R upper triangular
  * with positive diagonal; in place on n x m (m <= kt). A relative pivot R_ii / sqrt(G_ii) < 1e-7 counts as a
  * breakdown and the shifted CholeskyQR3 of Fukaya et al. (2020) is used instead. Synchronises the stream.
  * *fallback (may be NULL) is set to 1 when the fallback ran. Returns PPCG_ERR_BREAKDOWN if that failed too. */
 PPCG_API ppcg_status ppcg_cholqr2(ppcg_handle h, double* X, int64_t ldx, int32_t m, int32_t* fallback);
 
-/* Symmetric eigensolver of the Rayleigh-Ritz step (steps 23-24, Section 5.5): M is m x m (leading dimension m,
+/* Symmetric eigensolver of the Rayleigh-Ritz step (steps 23-24, Section 5.6): M is m x m (leading dimension m,
  * the upper triangle is read), lambda receives the m eigenvalues ascending and C (m x m) the orthonormal
  * eigenvectors as columns. M, lambda and C are device buffers owned by the caller; C must not overlap M.
  * Route: if no off-diagonal entry exceeds 1e-14 ||M||_F, the sorted diagonal and unit vectors. If none exceeds

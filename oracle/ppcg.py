@@ -29,10 +29,10 @@ Readings of the paper taken where it is silent (each is restated where it is use
   R7  stop test: r_i = ||A x_i - lambda_i x_i||_2 of the first k (non-buffer) Ritz pairs at a Rayleigh-Ritz
       step, max_i r_i <= tol; a Rayleigh-Ritz step is forced at once when ||W||_F <= tol after step 20.
   R8  locking: at every Rayleigh-Ritz step J_lock = {i < k : r_i <= tol}; locked vectors enter the next
-      Rayleigh-Ritz step through S = [X, X_lock] (soft locking, Section 5.6).
+      Rayleigh-Ritz step through S = [X, X_lock] (soft locking, Section 5.7).
   R9  output: Ritz values ascending; each Ritz vector has unit norm and its entry of largest modulus
       (lowest index on ties) real and positive.
-  R10 orthonormalisation variants of Section 5.4 (optional; the default is CholeskyQR2 every plain step):
+  R10 orthonormalisation variants of Section 5.5 (optional; the default is CholeskyQR2 every plain step):
       "polar" replaces step 18 by X <- X (X* X)^{-1/2}, the (X* X)^{-1/2} = (I + Y)^{-1/2} series in
       Y = X* X - I truncated after t terms, t the fewest (at most POLAR_MAX_TERMS) whose first omitted term
       |c_{t+1}| nu^{t+1} is below the FP64 unit roundoff, nu = ||Y||_F; when no such t exists (nu too large
@@ -139,7 +139,7 @@ def project(Y, X):
 
 
 def cholqr(X):
-    """Cholesky QR (Section 5.4): X*X = R*R with R upper triangular, positive diagonal; Q = X R^{-1}.
+    """Cholesky QR (Section 5.5): X*X = R*R with R upper triangular, positive diagonal; Q = X R^{-1}.
 
     Raises numpy.linalg.LinAlgError on a non-positive pivot.
     """
@@ -190,7 +190,7 @@ def orth(X, stats=None):
 
 
 def polar_coefficients(t):
-    """c_0..c_t of the binomial series (1 + y)^{-1/2} = sum_j c_j y^j, c_j = binom(-1/2, j) (Section 5.4)."""
+    """c_0..c_t of the binomial series (1 + y)^{-1/2} = sum_j c_j y^j, c_j = binom(-1/2, j) (Section 5.5)."""
     c = [1.0]
     for j in range(1, t + 1):
         c.append(c[-1] * (-(2 * j - 1) / (2 * j)))
@@ -209,7 +209,7 @@ def polar_terms(nu, tmax=POLAR_MAX_TERMS):
 
 
 def orth_polar(X, t):
-    """X <- X (I + Y)^{-1/2} with the series truncated after t terms, Y = X* X - I (Section 5.4)."""
+    """X <- X (I + Y)^{-1/2} with the series truncated after t terms, Y = X* X - I (Section 5.5)."""
     m = X.shape[1]
     Y = X.conj().T @ X - np.eye(m)
     c = polar_coefficients(t)

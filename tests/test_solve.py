@@ -153,7 +153,7 @@ def test_fp64_emulation_solve_grid16_k64(precision):
     _check_pairs(V, w.N, lam, X, w.tol)
 
 
-# ---------------------------------------------------------------- orthonormalisation variants (Section 5.4)
+# ---------------------------------------------------------------- orthonormalisation variants (Section 5.5)
 @pytest.mark.parametrize("orth,skip,precision,gemm", [
     ("polar", 0.0, "fp64", "fma"),
     ("cholqr2", 1e-14, "fp64", "fma"),
