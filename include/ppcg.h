@@ -4,8 +4,8 @@
  * Computes the k algebraically smallest eigenpairs of A = -Laplacian_h + diag(V) (7-point stencil on a periodic
  * nx x ny x nz grid) with the Projected Preconditioned Conjugate Gradient method of Vecharynski, Yang and Pask
  * (arXiv 1407.7506): the trace-minimisation problem of Section 2 (eq. tracemin), iterated as Algorithm 3
- * (Appendix A) with sub-block size sbsize (Section 5.1), Rayleigh-Ritz every rr_period iterations (Section 5.5),
- * soft locking (Section 5.6), buffer vectors (Section 5.3) and Cholesky QR orthonormalisation (Section 5.4).
+ * (Appendix A) with sub-block size sbsize (Section 5.1), Rayleigh-Ritz every rr_period iterations (Section 5.6),
+ * soft locking (Section 5.7), buffer vectors (Section 5.3) and Cholesky QR orthonormalisation (Section 5.5).
  *
  * Conventions
  *   - A grid function is n = nx*ny*nz doubles, linear index p = i + nx*j + nx*ny*l (x fastest).
@@ -65,21 +65,22 @@ typedef struct {
 typedef struct {
   int32_t maxiter;      /* [0 -> 500] iterations of the loop of Algorithm 3 */
   int32_t nbuf;         /* [0] buffer vectors (Section 5.3); X0 then has k + nbuf columns */
-  int32_t no_lock;      /* [0] 1 disables soft locking (Section 5.6) */
+  int32_t no_lock;      /* [0] 1 disables soft locking (Section 5.7) */
   int32_t precision;    /* [PPCG_FP64] ppcg_precision */
   double sigma_floor;   /* [0 -> 0.1/h^2] floor delta of the preconditioner diagonal, see ppcg_solve */
   int32_t timing;       /* [0] 1 records per-phase device times into ppcg_stats.t_phase_ms */
   int32_t history_cap;  /* [0] capacity (entries) of history */
-  double* history;      /* [NULL] host array of 4 * history_cap doubles; entry i = {iteration, kind,
-                           value, trace}: kind 0 = plain step (value = ||W||_F over the wanted columns),
-                           kind 1 = Rayleigh-Ritz step (value = max_i r_i, trace = sum of the k Ritz values) */
+  double* history;      /* [NULL] host array of 5 * history_cap doubles; entry i = {iteration, kind,
+                           value, trace, k_act}: kind 0 = plain step (value = ||W||_F over the wanted columns),
+                           kind 1 = Rayleigh-Ritz step (value = max_i r_i, trace = sum of the k Ritz values);
+                           k_act = active (unlocked) columns the iteration worked on (k + nbuf for iteration 0) */
   int32_t fp64_gemm;    /* [0] how the FP64 n x k GEMMs run: 0 = FP64 FMA pipe, 1 = FP64-accurate emulation on
                            the BF16 tensor cores (error-free splitting into 8 digit slices, Ozaki scheme) */
-  int32_t orth;         /* [0] step 18 (Section 5.4): 0 = CholeskyQR2; 1 = polar X <- X (X^T X)^{-1/2} by the
+  int32_t orth;         /* [0] step 18 (Section 5.5): 0 = CholeskyQR2; 1 = polar X <- X (X^T X)^{-1/2} by the
                            series of (I + Y)^{-1/2}, Y = X^T X - I, with the fewest terms (at most 8) whose first
                            omitted term nu^{t+1} |c_{t+1}| is below the FP64 unit roundoff, nu = ||Y||_F; when no
                            such t exists CholeskyQR2 runs instead */
-  double orth_skip_tol; /* [0] skip step 18 when ||X^T X - I||_F <= orth_skip_tol (Section 5.4); 0 never skips */
+  double orth_skip_tol; /* [0] skip step 18 when ||X^T X - I||_F <= orth_skip_tol (Section 5.5); 0 never skips */
   int32_t reserved[2];
 } ppcg_options;
 
@@ -104,7 +105,9 @@ typedef struct {
   int32_t n_orth_skip;        /* plain steps whose orthonormalisation was skipped (options.orth_skip_tol) */
   int32_t n_polar;            /* plain steps orthonormalised by the polar series (options.orth = 1) */
   int32_t n_eig_diagonal;     /* Rayleigh-Ritz eigensolves whose matrix was already diagonal (no rotation needed) */
-  int32_t n_eig_refined;      /* Rayleigh-Ritz eigensolves finished by eigenvector refinement instead of Jacobi */
+  int32_t n_eig_refined;      /* Rayleigh-Ritz eigensolves finished by eigenvector refinement from the identity */
+  int32_t n_eig_mixed;        /* Rayleigh-Ritz eigensolves by single-precision Jacobi + FP64 eigenvector refinement
+                                 (the others that are not diagonal, refined or mixed took FP64 Jacobi) */
 } ppcg_stats;
 
 typedef struct ppcg_ctx* ppcg_handle;
@@ -121,7 +124,7 @@ PPCG_API ppcg_status ppcg_workspace_bytes(const ppcg_operator* op, int64_t n, in
  *   n           must equal nx*ny*nz
  *   k           1 <= k, k + nbuf <= n/2
  *   sbsize      sub-block size q of Section 5.1, 1 <= sbsize <= min(k + nbuf, 16) (8 for PPCG_C128)
- *   rr_period   Rayleigh-Ritz period (Section 5.5), >= 1
+ *   rr_period   Rayleigh-Ritz period (Section 5.6), >= 1
  *   opt         may be NULL (defaults)
  *   cuda_stream a cudaStream_t (NULL = legacy default stream)
  *   workspace   device memory of at least ppcg_workspace_bytes, owned by the caller and kept alive until
@@ -183,7 +186,7 @@ typedef struct {
 PPCG_API ppcg_status ppcg_solve_batched(ppcg_batch_item* items, int32_t count, int32_t max_concurrent);
 
 /*
- * Autotuner for the sub-block size q (Section 5.1; the paper's sbsize experiments in Section 7 show that the
+ * Autotuner for the sub-block size q (Section 5.1; the paper's sbsize experiments in Section 6.1 show that the
  * best q depends on the problem). For each candidate q in candidates[0..ncand) with 1 <= q <= min(k + nbuf, 16)
  * it creates a solver (library-allocated workspace), solves from X0 to tol on cuda_stream and times the solve
  * with CUDA events; time_ms[i] receives the time (a negative value for a candidate that was invalid or did not

@@ -74,6 +74,14 @@ PPCG_API ppcg_status ppcg_residual(ppcg_handle h, const double* X, const double*
 PPCG_API ppcg_status ppcg_energy_gradient(ppcg_handle h, const double* X, int64_t ld, int32_t k, double scale,
                                           double* grad_V);
 
+/* Check of the bounded device-side waits (the paper has no counterpart; failure handling of this library): runs a
+ * cooperative kernel on the handle's stream in which one CTA never reaches the grid barrier that the others wait
+ * at, with the wait bounded by spin_polls polls (>= 32; the solver's own barriers allow 2^22). The waiting CTAs
+ * give up and return, so the call returns PPCG_ERR_TIMEOUT, the status a solve reports when one of its grid
+ * barriers gives up, and the handle stays usable. Returns PPCG_OK only if the wait unexpectedly completed, and
+ * PPCG_ERR_ARG for a NULL handle or spin_polls < 32. Synchronises the stream. */
+PPCG_API ppcg_status ppcg_barrier_timeout_check(ppcg_handle h, int32_t spin_polls);
+
 /* Gram matrix C = A^T B without a handle and without allocating any device memory. The paper has no
  * counterpart: this entry point exists for callers that cannot allocate (a fixed device-memory budget, an
  * application memory pool that forbids cudaMalloc, no ppcg handle). A is n x ma (lda >= n), B is n x mb

@@ -27,7 +27,7 @@ PHASES = ("AX", "GEMM", "BlockRR", "CholQR", "RR", "Precond", "Lock", "Other")
 EXPORTS = ("ppcg_status_string", "ppcg_workspace_bytes", "ppcg_create", "ppcg_set_potential", "ppcg_solve",
            "ppcg_destroy", "ppcg_apply_operator", "ppcg_gram", "ppcg_project", "ppcg_cholqr2", "ppcg_dense_eigh",
            "ppcg_block_coefficients", "ppcg_block_update", "ppcg_residual", "ppcg_gram_noalloc",
-           "ppcg_energy_gradient", "ppcg_solve_batched", "ppcg_autotune_sbsize")
+           "ppcg_energy_gradient", "ppcg_solve_batched", "ppcg_autotune_sbsize", "ppcg_barrier_timeout_check")
 
 
 class ppcg_operator(ctypes.Structure):
@@ -49,7 +49,7 @@ class ppcg_stats(ctypes.Structure):
                 ("n_early_rr", ctypes.c_int32), ("converged", ctypes.c_int32), ("history_len", ctypes.c_int32),
                 ("jacobi_sweeps_max", ctypes.c_int32), ("kernel_launches", ctypes.c_int64), ("t_phase_ms", ctypes.c_double * 8),
                 ("max_res", ctypes.c_double), ("n_orth_skip", ctypes.c_int32), ("n_polar", ctypes.c_int32),
-                ("n_eig_diagonal", ctypes.c_int32), ("n_eig_refined", ctypes.c_int32)]
+                ("n_eig_diagonal", ctypes.c_int32), ("n_eig_refined", ctypes.c_int32), ("n_eig_mixed", ctypes.c_int32)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "t_phase_ms"}
@@ -103,6 +103,7 @@ def lib():
             "ppcg_solve_batched": (_i32, [P(ppcg_batch_item), _i32, _i32]),
             "ppcg_autotune_sbsize": (_i32, [P(ppcg_operator), _i64, _i32, _i32, P(ppcg_options), _vp, _d,
                                             P(_i32), _i32, _vp, P(_i32), P(_d)]),
+            "ppcg_barrier_timeout_check": (_i32, [_vp, _i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -189,6 +190,11 @@ def ppcg_residual(h, X, HX, ld, m, M, lam, sigma, W, colnorm2):
 
 def ppcg_energy_gradient(h, X, ld, k, scale, grad_V):
     _check(lib().ppcg_energy_gradient(h, X, ld, k, scale, grad_V), "ppcg_energy_gradient")
+
+
+def ppcg_barrier_timeout_check(h, spin_polls):
+    """Returns the status (PPCG_ERR_TIMEOUT when the bounded barrier wait gave up as designed)."""
+    return lib().ppcg_barrier_timeout_check(h, spin_polls)
 
 
 def ppcg_gram_noalloc(A, lda, B, ldb, n, ma, mb, C, stream=0):

@@ -41,6 +41,7 @@ struct ppcg_ctx {
   double* blk[7] = {};
   double *X = nullptr, *Xs = nullptr, *HX = nullptr, *W = nullptr, *HW = nullptr, *P = nullptr, *HP = nullptr;
   double *G = nullptr, *M = nullptr, *C = nullptr, *Rinv = nullptr, *lam = nullptr, *norms = nullptr;
+  double* lamlk = nullptr;    // Ritz values of the locked columns (their Rayleigh-Ritz step), leading kl entries
   double *normpart = nullptr, *gpart = nullptr, *bpart = nullptr, *coef = nullptr, *cholws = nullptr,
          *jacws = nullptr;
   size_t gpart_cap = 0, bpart_cap = 0;
@@ -55,8 +56,8 @@ struct ppcg_ctx {
   size_t evused = 0;
   double t_ms[8] = {};
   int last_sweeps = 0;
-  int eig_path = 0;           // route of the last dense_eigh: 0 Jacobi, 1 diagonal, 2 refined
-  int eig_count[3] = {0, 0, 0};   // dense_eigh calls of the current solve per route
+  int eig_path = 0;           // route of the last dense_eigh: 0 Jacobi, 1 diagonal, 2 refined, 3 FP32 + refined
+  int eig_count[4] = {0, 0, 0, 0};   // dense_eigh calls of the current solve per route
   bool mixed = false;      // PPCG_MIXED_TF32: projections and the first CholQR Gram on tcgen05
   bool ozaki = false;      // FP64 n x k GEMMs emulated on the BF16 tensor cores (error-free splitting)
   int* ozexps = nullptr;   // exponent workspace of the emulated GEMMs
@@ -108,7 +109,7 @@ Sizes make_sizes(int64_t n, int kt, int q, bool ozaki) {
 
 // Offsets of every region; returns the total byte count.
 struct Offsets {
-  size_t V, dg, blk[7], G, M, C, Rinv, lam, norms, normpart, gpart, bpart, coef, cholws, jacws;
+  size_t V, dg, blk[7], G, M, C, Rinv, lam, lamlk, norms, normpart, gpart, bpart, coef, cholws, jacws;
   size_t iflag, icnt, jinfo, idx, bflags, bar, ozexps, ozimg;
   size_t total;
 };
@@ -126,6 +127,7 @@ Offsets layout(const Sizes& s) {
   o.C = L.off(kk, 8);
   o.Rinv = L.off(kk, 8);
   o.lam = L.off(s.kt, 8);
+  o.lamlk = L.off(s.kt, 8);
   o.norms = L.off(s.kt, 8);
   o.normpart = L.off((size_t)norm_row_tiles(s.n) * s.kt, 8);
   o.gpart = L.off(s.gpart_cap, 8);
@@ -338,15 +340,19 @@ ppcg_status cholqr2(ppcg_ctx* c, double* X, int64_t ldx, double* Xs, int64_t ldx
   return PPCG_OK;
 }
 
+// how the k x k products run: on the tensor cores (Ozaki) whenever the n x k GEMMs do
+KxK kxk(ppcg_ctx* c) {
+  return KxK{c->gpart, c->gpart_cap, c->ozaki, c->ozexps, c->ozimg, c->ozimg_bytes, c->tcflag};
+}
+
 // Mm must not alias c->G (the symmetrisation scratch) or Cm
 ppcg_status dense_eigh(ppcg_ctx* c, const double* Mm, int m, double* lam, double* Cm) {
   CK(cudaMemsetAsync(c->iflag, 0, sizeof(int), c->stream));
   CK(cudaMemsetAsync(c->jinfo, 0, 2 * sizeof(int), c->stream));
   int path = 0;
-  CK(dense_eigh_auto(Mm, m, lam, Cm, c->jacws, c->G, c->gpart, c->gpart_cap, c->iflag, c->bar, c->jinfo, &path,
-                     c->stream));
+  CK(dense_eigh_auto(Mm, m, lam, Cm, c->jacws, c->G, kxk(c), c->iflag, c->bar, c->jinfo, &path, c->stream));
   c->eig_path = path;
-  if (path >= 0 && path < 3) c->eig_count[path]++;
+  if (path >= 0 && path < 4) c->eig_count[path]++;
   return PPCG_OK;
 }
 
@@ -369,7 +375,7 @@ int polar_terms(double nu, double* coef) {
   return 0;
 }
 
-// Step 18 with the variants of Section 5.4: CholeskyQR2, the polar series X (I + Y)^{-1/2} (Y = X^T X - I, FP64
+// Step 18 with the variants of Section 5.5: CholeskyQR2, the polar series X (I + Y)^{-1/2} (Y = X^T X - I, FP64
 // Gram in every form), or no orthonormalisation when ||Y||_F <= orth_skip_tol.
 ppcg_status orthonormalize(ppcg_ctx* c, double* X, int64_t ldx, double* Xs, int64_t ldxs, int m, ppcg_stats* S) {
   const bool variant = c->opt.orth != 0 || c->opt.orth_skip_tol > 0.0;
@@ -393,7 +399,7 @@ ppcg_status orthonormalize(ppcg_ctx* c, double* X, int64_t ldx, double* Xs, int6
       double* Zn = c->Rinv;
       CK(scaled_plus_identity(c->G, m, coef[t], coef[t - 1], Z, c->stream));
       for (int j = t - 2; j >= 0; --j) {
-        CK(small_gemm(false, c->G, m, Z, m, m, m, m, Zn, m, c->gpart, c->gpart_cap, c->stream));
+        CK(kxk_gemm(kxk(c), false, c->G, m, Z, m, m, m, m, Zn, m, c->stream));
         CK(add_diag(Zn, m, coef[j], c->stream));
         std::swap(Z, Zn);
       }
@@ -437,22 +443,36 @@ struct SolveState {
 
 // Steps 22-31: Rayleigh-Ritz on S = [X_lock, X_act], residuals, stop test, locking and compaction.
 // Step 23 solves eq. projev on S as written: with S^T S = R^T R (Cholesky), K = R^{-T} (S^T A S) R^{-1} is
-// diagonalised by Jacobi, K Z = Z Omega, and X = S (R^{-1} Z). If that Cholesky breaks down (relative pivot below
+// diagonalised, K Z = Z Omega, and X = S (R^{-1} Z). If that Cholesky breaks down (relative pivot below
 // kCholPivotTol), S is orthonormalised by CholeskyQR2 first and the standard problem Q^T A Q is solved instead.
+// The locked columns are orthonormal Ritz vectors of the previous Rayleigh-Ritz step that no step has touched
+// since (steps 9-20 act on the active columns only), so the locked block of S^T S is I and that of S^T A S is
+// diag(Lambda_lock) in exact arithmetic: only S^T X_act and S^T (A X_act) are formed, n k_t k_act work instead of
+// the full Grams' n k_t^2 (most columns are locked late in a solve).
 ppcg_status rr_step(ppcg_ctx* c, SolveState& st, bool allow_compact, ppcg_stats* stats, double tol) {
   const int kt = c->kt;
   cudaStream_t s = c->stream;
   int* rrflag = c->icnt + 3;
+  const int kl = st.k_lock < kt ? st.k_lock : 0;
   phase_mark(c, PPCG_T_AX);
-  PS(apply_H(c, c->X, c->ld, c->HX, c->ld, kt));
+  if (kl > 0) PS(apply_H(c, c->X + (int64_t)kl * c->ld, c->ld, c->HX + (int64_t)kl * c->ld, c->ld, kt - kl));
+  else PS(apply_H(c, c->X, c->ld, c->HX, c->ld, kt));
   phase_mark(c, PPCG_T_RR);
-  PS(gram(c, c->X, c->ld, c->X, c->ld, kt, kt, c->G, kt));              // S^T S
-  PS(gram(c, c->X, c->ld, c->HX, c->ld, kt, kt, c->M, kt));             // S^T A S
+  if (kl > 0) {
+    const double* Xa = c->X + (int64_t)kl * c->ld;
+    const double* HXa = c->HX + (int64_t)kl * c->ld;
+    PS(gram(c, c->X, c->ld, Xa, c->ld, kt, kt - kl, c->G + (int64_t)kl * kt, kt));    // S^T X_act
+    PS(gram(c, c->X, c->ld, HXa, c->ld, kt, kt - kl, c->M + (int64_t)kl * kt, kt));   // S^T A X_act
+    CK(locked_gram_fill(c->G, c->M, kt, kl, c->lamlk, s));
+  } else {
+    PS(gram(c, c->X, c->ld, c->X, c->ld, kt, kt, c->G, kt));            // S^T S
+    PS(gram(c, c->X, c->ld, c->HX, c->ld, kt, kt, c->M, kt));           // S^T A S
+  }
   CK(cudaMemsetAsync(rrflag, 0, sizeof(int), s));
   CK(chol_inv(c->G, kt, 0.0, c->Rinv, c->cholws, rrflag, c->bar, s));  // R^{-1}
   // K = R^{-T} (S^T A S) R^{-1}: T = (S^T A S) R^{-1} (R^{-1} upper: trimmed K loop), K = (R^{-1})^T T
-  CK(small_gemm(false, c->M, kt, c->Rinv, kt, kt, kt, kt, c->G, kt, c->gpart, c->gpart_cap, s));
-  CK(small_gemm(true, c->Rinv, kt, c->G, kt, kt, kt, kt, c->M, kt, c->gpart, c->gpart_cap, s));
+  CK(kxk_gemm(kxk(c), false, c->M, kt, c->Rinv, kt, kt, kt, kt, c->G, kt, s));
+  CK(kxk_gemm(kxk(c), true, c->Rinv, kt, c->G, kt, kt, kt, kt, c->M, kt, s));
   PS(dense_eigh(c, c->M, kt, c->lam, c->C));
   // sigma = smallest Ritz value of this step: the host needs it for the preconditioner
   CK(cudaMemcpyAsync(c->lam_h.data(), c->lam, sizeof(double) * kt, cudaMemcpyDeviceToHost, s));
@@ -477,7 +497,7 @@ ppcg_status rr_step(ppcg_ctx* c, SolveState& st, bool allow_compact, ppcg_stats*
     if (fl[0] & kFlagTimeout) return PPCG_ERR_TIMEOUT;
   } else {
     // coefficients R^{-1} Z (R^{-1} is upper triangular)
-    CK(small_gemm(false, c->Rinv, kt, c->C, kt, kt, kt, kt, c->G, kt, c->gpart, c->gpart_cap, s));
+    CK(kxk_gemm(kxk(c), false, c->Rinv, kt, c->C, kt, kt, kt, kt, c->G, kt, s));
   }
   PS(update(c, c->X, c->ld, c->G, kt, kt, kt, c->Xs, c->ld, Epi::Store, false));
   swap(c->X, c->Xs);
@@ -521,6 +541,10 @@ ppcg_status rr_step(ppcg_ctx* c, SolveState& st, bool allow_compact, ppcg_stats*
       if (it != st.pos_act.end()) pidx[j] = (int)(it - st.pos_act.begin());
     }
   }
+  std::vector<double> lam_lock(nl > 0 ? nl : 1);
+  for (int i = 0; i < nl; ++i) lam_lock[i] = c->lam_h[lock[i]];
+  if (nl > 0)
+    CK(cudaMemcpyAsync(c->lamlk, lam_lock.data(), sizeof(double) * nl, cudaMemcpyHostToDevice, c->stream));
   int* d_order = c->idx;
   CK(cudaMemcpyAsync(d_order, order.data(), sizeof(int) * kt, cudaMemcpyHostToDevice, c->stream));
   CK(gather_cols(c->X, c->ld, c->Xs, c->ld, c->n, d_order, kt, c->stream));
@@ -544,13 +568,14 @@ ppcg_status rr_step(ppcg_ctx* c, SolveState& st, bool allow_compact, ppcg_stats*
   return PPCG_OK;
 }
 
-void record(ppcg_ctx* c, ppcg_stats* S, int it, int kind, double value, double trace) {
+void record(ppcg_ctx* c, ppcg_stats* S, int it, int kind, double value, double trace, int k_act) {
   if (!c->opt.history || S->history_len >= c->opt.history_cap) return;
-  double* e = c->opt.history + 4 * (size_t)S->history_len;
+  double* e = c->opt.history + 5 * (size_t)S->history_len;
   e[0] = it;
   e[1] = kind;
   e[2] = value;
   e[3] = trace;
+  e[4] = k_act;
   S->history_len++;
 }
 
@@ -660,7 +685,7 @@ ppcg_status ppcg_create(const ppcg_operator* op, int64_t n, int32_t k, int32_t s
   c->X = c->blk[0]; c->Xs = c->blk[1]; c->HX = c->blk[2]; c->W = c->blk[3];
   c->HW = c->blk[4]; c->P = c->blk[5]; c->HP = c->blk[6];
   c->G = D(o.G); c->M = D(o.M); c->C = D(o.C); c->Rinv = D(o.Rinv);
-  c->lam = D(o.lam); c->norms = D(o.norms); c->normpart = D(o.normpart);
+  c->lam = D(o.lam); c->lamlk = D(o.lamlk); c->norms = D(o.norms); c->normpart = D(o.normpart);
   c->gpart = D(o.gpart); c->bpart = D(o.bpart); c->coef = D(o.coef);
   c->cholws = D(o.cholws); c->jacws = D(o.jacws);
   c->iflag = I(o.iflag); c->icnt = I(o.icnt); c->jinfo = I(o.jinfo); c->idx = I(o.idx); c->bflags = I(o.bflags);
@@ -706,7 +731,7 @@ ppcg_status ppcg_solve(ppcg_handle c, const double* X0, double tol, double* lamb
   ppcg_stats local{};
   ppcg_stats* S = stats ? stats : &local;
   std::memset(S, 0, sizeof(*S));
-  c->eig_count[0] = c->eig_count[1] = c->eig_count[2] = 0;
+  c->eig_count[0] = c->eig_count[1] = c->eig_count[2] = c->eig_count[3] = 0;
   std::memset(c->t_ms, 0, sizeof(c->t_ms));
   c->evused = 0;
   const long long launches0 = launch_count();
@@ -735,7 +760,7 @@ ppcg_status ppcg_solve(ppcg_handle c, const double* X0, double tol, double* lamb
   // Rayleigh-Ritz on orth(X0) before iteration 1 (provides sigma and the Ritz residual W)
   const int maxiter = c->opt.maxiter;
   PS(rr_step(c, st, maxiter > 0, S, tol));
-  record(c, S, 0, 1, st.max_res, ritz_trace(c));
+  record(c, S, 0, 1, st.max_res, ritz_trace(c), kt);
   if (st.pos_act.empty()) {
     st.pos_act.resize(st.k_act);
     for (int j = 0; j < st.k_act; ++j) st.pos_act[j] = j;
@@ -784,7 +809,7 @@ ppcg_status ppcg_solve(ppcg_handle c, const double* X0, double tol, double* lamb
         if (!std::isfinite(c->nrm_h[j])) return PPCG_ERR_NUMERIC;
         if (st.pos_act[j] < c->k) wf2 += c->nrm_h[j];
       }
-      record(c, S, it, 0, std::sqrt(wf2), 0.0);
+      record(c, S, it, 0, std::sqrt(wf2), 0.0, ka);
       if (std::sqrt(wf2) <= tol) {
         do_rr = true;            // forced Rayleigh-Ritz step: ||W||_F <= tol bounds every Ritz residual
         S->n_early_rr++;
@@ -793,14 +818,14 @@ ppcg_status ppcg_solve(ppcg_handle c, const double* X0, double tol, double* lamb
     if (do_rr) {
       // steps 22-31
       PS(rr_step(c, st, it < maxiter, S, tol));
-      record(c, S, it, 1, st.max_res, ritz_trace(c));
+      record(c, S, it, 1, st.max_res, ritz_trace(c), ka);
       last_rr = true;
     }
   }
   if (!last_rr) {
     // step 32: final Rayleigh-Ritz (no compaction: X ends in ascending Ritz order)
     PS(rr_step(c, st, false, S, tol));
-    record(c, S, it, 1, st.max_res, ritz_trace(c));
+    record(c, S, it, 1, st.max_res, ritz_trace(c), st.k_act);
   }
   // outputs: first k Ritz pairs, phase convention, residuals recomputed on the returned vectors
   phase_mark(c, PPCG_T_OTHER);
@@ -847,6 +872,7 @@ ppcg_status ppcg_solve(ppcg_handle c, const double* X0, double tol, double* lamb
   S->kernel_launches = launch_count() - launches0;
   S->n_eig_diagonal = c->eig_count[1];
   S->n_eig_refined = c->eig_count[2];
+  S->n_eig_mixed = c->eig_count[3];
   for (int i = 0; i < 8; ++i) S->t_phase_ms[i] = c->t_ms[i];
   return st.done ? PPCG_OK : PPCG_ERR_NOT_CONVERGED;
 }
@@ -882,12 +908,25 @@ ppcg_status ppcg_cholqr2(ppcg_handle c, double* X, int64_t ldx, int32_t m, int32
 
 ppcg_status ppcg_dense_eigh(ppcg_handle c, const double* M, int32_t m, double* lambda, double* C) {
   if (!c || !M || !lambda || !C || m < 1 || m > c->kt) return PPCG_ERR_ARG;
+  CK(cudaMemsetAsync(c->tcflag, 0, sizeof(int), c->stream));
   PS(dense_eigh(c, M, m, lambda, C));
   c->last_sweeps = last_sweeps(c);
   const int f = read_flag(c);
+  int ft = 0;
+  CK(cudaMemcpyAsync(&ft, c->tcflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   if (f < 0) return PPCG_ERR_CUDA;
-  if (f & kFlagTimeout) return PPCG_ERR_TIMEOUT;
+  if ((f | ft) & kFlagTimeout) return PPCG_ERR_TIMEOUT;
   return PPCG_OK;
+}
+
+ppcg_status ppcg_barrier_timeout_check(ppcg_handle c, int32_t spin_polls) {
+  if (!c || spin_polls < 32) return PPCG_ERR_ARG;
+  CK(cudaMemsetAsync(c->iflag, 0, sizeof(int), c->stream));
+  CK(barrier_timeout_probe(spin_polls, c->iflag, c->bar, c->stream));
+  const int f = read_flag(c);
+  if (f < 0) return PPCG_ERR_CUDA;
+  return (f & kFlagTimeout) ? PPCG_ERR_TIMEOUT : PPCG_OK;
 }
 
 ppcg_status ppcg_block_coefficients(ppcg_handle c, const double* X, const double* W, const double* P,

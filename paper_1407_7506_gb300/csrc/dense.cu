@@ -1,9 +1,9 @@
 // Dense k x k kernels of Algorithm 3 (the ScaLAPACK part of Section 6):
-//   chol_inv     R^{-1} for the Cholesky factor of the Gram X^T X = R^T R (CholQR, Section 5.4, steps 18-19):
+//   chol_inv     R^{-1} for the Cholesky factor of the Gram X^T X = R^T R (CholQR, Section 5.5, steps 18-19):
 //                blocked right-looking Cholesky on 32 x 32 tiles with the inverse of L = R^T formed in the
 //                same sweep; one cooperative persistent kernel, quarter-tile tasks spread over the CTAs.
 //   jacobi_eigh  eigen-decomposition of the projected matrix of the Rayleigh-Ritz step (steps 23-24,
-//                Section 5.5): parallel cyclic Jacobi with round-robin pairing. In every round each 2 x 2 block
+//                Section 5.6): parallel cyclic Jacobi with round-robin pairing. In every round each 2 x 2 block
 //                of A is rotated from both sides independently (ping-pong buffers), each CTA recomputing the
 //                rotations it needs from the previous round's matrix, so one grid barrier separates rounds.
 // On GB300 FP64 is scarce (2 DFMA lanes per clock per SM); these kernels spread the O(k^3) work over all SMs
@@ -43,7 +43,8 @@ __device__ __forceinline__ void red_release_gpu(unsigned* p, unsigned v) {
 // fire-and-forget release add and waiting is polling with acquire loads (no return trip on arrival, no release
 // store by a last arriver). Every CTA tracks g locally in `gen`. The wait is bounded: after kSpinLimit polls the
 // CTA sets kFlagTimeout and every CTA returns false.
-__device__ bool grid_sync(unsigned* bar, unsigned nblocks, int* flag, unsigned& gen) {
+__device__ bool grid_sync(unsigned* bar, unsigned nblocks, int* flag, unsigned& gen,
+                          long long spin_limit = kSpinLimit) {
   __shared__ int ok;
   gen += 1u;
   __syncthreads();
@@ -56,7 +57,7 @@ __device__ bool grid_sync(unsigned* bar, unsigned nblocks, int* flag, unsigned& 
     int good = 1;
     long long spins = 0;
     while ((int)(ld_acquire_gpu(bar) - target) < 0) {
-      if ((++spins & 31) == 0 && (spins > kSpinLimit || (ld_relaxed_gpu(flag) & kFlagTimeout))) {
+      if ((++spins & 31) == 0 && (spins > spin_limit || (ld_relaxed_gpu(flag) & kFlagTimeout))) {
         atomicOr(flag, kFlagTimeout);
         good = 0;
         break;
@@ -252,13 +253,17 @@ chol_inv_kernel(const double* __restrict__ G, int m, int mp, double shift, doubl
 // per thread) and V tiles of 64 rows x 16 column pairs. A tile needs 32 rotations and a V tile 16; one warp
 // computes them into shared memory while the other threads load their blocks, so each rotation is formed once per
 // tile instead of once per block.
+//
+// The kernel runs in FP64 (the eigensolve of last resort, accurate to a few ulps of ||A||) and in FP32, where it
+// only supplies the starting eigenvectors of the FP64 refinement below: FP32 arithmetic runs on the 64x wider FP32
+// pipe, and the matrix and vectors take half the memory traffic.
 constexpr int JR = 16;   // row pairs per A tile
 constexpr int JC = 16;   // column pairs per A tile and per V tile
 constexpr int JV = 64;   // rows per V tile
 
 __device__ __forceinline__ int slot_shift(int t, int mp) { return t == 0 ? 0 : (t == mp - 1 ? 1 : t + 1); }
 
-// Rotation (c, s) that annihilates apq approximately: t = tan(phi) from a single-precision solve of
+// FP64 rotation (c, s) that annihilates apq approximately: t = tan(phi) from a single-precision solve of
 // t^2 + 2 theta t - 1 = 0, theta = (aqq - app) / (2 apq), then c = 1/sqrt(1 + t^2) refined by two FP64 Newton
 // steps and s = t c, so that c^2 + s^2 = 1 to FP64 rounding and the rotation is an exact orthogonal similarity.
 // theta is divided in single precision from operands scaled by inv = 1/||A||_F: |aqq - app| inv <= 2 and
@@ -284,22 +289,35 @@ __device__ __forceinline__ void rot_from(double app, double aqq, double apq, dou
   s = t * r;
 }
 
-__global__ void jacobi_init_kernel(const double* __restrict__ M, int m, int mp, double* A0, double* V0, double* Dg,
-                                   double* Od) {
+// FP32 rotation: the same angle, all in single precision
+__device__ __forceinline__ void rot_from(float app, float aqq, float apq, float thr, float, float& c, float& s) {
+  c = 1.0f; s = 0.0f;
+  if (!(fabsf(apq) > thr)) return;
+  const float th = (aqq - app) / (apq + apq);
+  const float at = fabsf(th);
+  float t = at > 1e18f ? 0.5f / at : 1.0f / (at + sqrtf(fmaf(at, at, 1.0f)));
+  if (th < 0.0f) t = -t;
+  c = rsqrtf(fmaf(t, t, 1.0f));
+  s = t * c;
+}
+
+template <typename T>
+__global__ void jacobi_init_kernel(const double* __restrict__ M, int m, int mp, T* A0, T* V0, T* Dg, T* Od) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)mp * mp;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % mp), j = (int)(e / mp);
-    const double v = (i < m && j < m) ? M[(i < j ? i : j) + (int64_t)(i < j ? j : i) * m] : 0.0;
+    const T v = (T)((i < m && j < m) ? M[(i < j ? i : j) + (int64_t)(i < j ? j : i) * m] : 0.0);
     A0[e] = v;
-    V0[e] = (i == j) ? 1.0 : 0.0;
+    V0[e] = (T)((i == j) ? 1.0 : 0.0);
     if (i == j) Dg[i] = v;
     if (i + j == mp - 1 && i < j) Od[i] = v;
   }
 }
 
-__global__ void frob_kernel(const double* __restrict__ A, int64_t cnt, double* out) {
+template <typename T>
+__global__ void frob_kernel(const T* __restrict__ A, int64_t cnt, double* out) {
   double s = 0.0;
-  for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) s += A[e] * A[e];
+  for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) s += (double)A[e] * (double)A[e];
   __shared__ double red[1024];
   red[threadIdx.x] = s;
   __syncthreads();
@@ -310,18 +328,22 @@ __global__ void frob_kernel(const double* __restrict__ A, int64_t cnt, double* o
   if (threadIdx.x == 0) out[0] = sqrt(red[0]);
 }
 
+template <typename T>
 struct JacBuf {
-  double *A[2], *V[2], *Dg[2], *Od[2];
+  T *A[2], *V[2], *Dg[2], *Od[2];
 };
 
-// Sweeps until the matrix left by a sweep has no off-diagonal entry above the threshold (then the next sweep
-// would rotate nothing, so it is not run). The test is taken in the last round of each sweep, whose output is
-// the whole matrix in identity layout.
+// Sweeps until the matrix left by a sweep has no off-diagonal entry above tol ||A||_F (then the next sweep would
+// rotate nothing, so it is not run), at most max_sweeps. The test is taken in the last round of each sweep, whose
+// output is the whole matrix in identity layout. Only the FP64 kernel reports non-convergence: the FP32 result is
+// a starting point whose accuracy the refinement measures itself.
+template <typename T>
 __global__ void __launch_bounds__(256)
-jacobi_kernel(JacBuf b, int m, int mp, const double* normA, int* counts, int* flag, unsigned* bar, int* info) {
+jacobi_kernel(JacBuf<T> b, int m, int mp, const double* normA, double tol, int max_sweeps, int* counts, int* flag,
+              unsigned* bar, int* info) {
   const double nrm = normA[0];
-  const double thr = kJacobiTol * nrm;
-  const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  const T thr = (T)(tol * nrm);
+  const T inv = (T)(nrm > 0.0 ? 1.0 / nrm : 0.0);
   const int P = mp / 2;
   const int TA = P / JR;
   const int nTA = TA * TA;
@@ -329,29 +351,29 @@ jacobi_kernel(JacBuf b, int m, int mp, const double* normA, int* counts, int* fl
   const int nT = nTA + nVR * (P / JC);
   const unsigned nb = gridDim.x;
   const int t = threadIdx.x;
-  __shared__ double rc[JR + JC], rs[JR + JC];
+  __shared__ T rc[JR + JC], rs[JR + JC];
   int cur = 0;
   int sweep = 0;
   bool converged = false;
   unsigned gen = 0;
-  while (sweep < kJacobiMaxSweeps && !converged) {
+  while (sweep < max_sweeps && !converged) {
     for (int r = 0; r < mp - 1; ++r) {
       const bool last = (r == mp - 2);
-      const double* __restrict__ A = cur ? b.A[1] : b.A[0];
-      double* __restrict__ An = cur ? b.A[0] : b.A[1];
-      const double* __restrict__ V = cur ? b.V[1] : b.V[0];
-      double* __restrict__ Vn = cur ? b.V[0] : b.V[1];
-      const double* __restrict__ Dg = cur ? b.Dg[1] : b.Dg[0];
-      const double* __restrict__ Od = cur ? b.Od[1] : b.Od[0];
-      double* __restrict__ Dn = cur ? b.Dg[0] : b.Dg[1];
-      double* __restrict__ On = cur ? b.Od[0] : b.Od[1];
+      const T* __restrict__ A = cur ? b.A[1] : b.A[0];
+      T* __restrict__ An = cur ? b.A[0] : b.A[1];
+      const T* __restrict__ V = cur ? b.V[1] : b.V[0];
+      T* __restrict__ Vn = cur ? b.V[0] : b.V[1];
+      const T* __restrict__ Dg = cur ? b.Dg[1] : b.Dg[0];
+      const T* __restrict__ Od = cur ? b.Od[1] : b.Od[0];
+      T* __restrict__ Dn = cur ? b.Dg[0] : b.Dg[1];
+      T* __restrict__ On = cur ? b.Od[0] : b.Od[1];
       int big = 0;
       for (int tile = blockIdx.x; tile < nT; tile += nb) {
         if (tile < nTA) {
           const int R0 = (tile % TA) * JR, C0 = (tile / TA) * JC;
           const int ri = R0 + (t % JR), ci = C0 + (t / JR);   // row pair ri, column pair ci
           const int rb = mp - 1 - ri, cb = mp - 1 - ci;
-          double x00, x01, x10, x11;        // rows (ri, rb) x cols (ci, cb)
+          T x00, x01, x10, x11;             // rows (ri, rb) x cols (ci, cb)
           if (ri == ci) {
             x00 = __ldcg(Dg + ri); x11 = __ldcg(Dg + rb); x01 = __ldcg(Od + ri); x10 = x01;
           } else {
@@ -360,17 +382,17 @@ jacobi_kernel(JacBuf b, int m, int mp, const double* normA, int* counts, int* fl
           }
           if (t < JR + JC) {
             const int p = t < JR ? R0 + t : C0 + (t - JR);
-            double c, s;
+            T c, s;
             rot_from(__ldcg(Dg + p), __ldcg(Dg + mp - 1 - p), __ldcg(Od + p), thr, inv, c, s);
             rc[t] = c;
             rs[t] = s;
           }
           __syncthreads();
-          const double cr = rc[t % JR], sr = rs[t % JR], cc = rc[JR + t / JR], sc = rs[JR + t / JR];
-          const double y00 = cr * x00 - sr * x10, y01 = cr * x01 - sr * x11;
-          const double y10 = sr * x00 + cr * x10, y11 = sr * x01 + cr * x11;
-          double z00 = cc * y00 - sc * y01, z01 = sc * y00 + cc * y01;
-          double z10 = cc * y10 - sc * y11, z11 = sc * y10 + cc * y11;
+          const T cr = rc[t % JR], sr = rs[t % JR], cc = rc[JR + t / JR], sc = rs[JR + t / JR];
+          const T y00 = cr * x00 - sr * x10, y01 = cr * x01 - sr * x11;
+          const T y10 = sr * x00 + cr * x10, y11 = sr * x01 + cr * x11;
+          T z00 = cc * y00 - sc * y01, z01 = sc * y00 + cc * y01;
+          T z10 = cc * y10 - sc * y11, z11 = sc * y10 + cc * y11;
           if (ri == ci) z10 = z01;                   // keep the diagonal block exactly symmetric
           const int R0s = slot_shift(ri, mp), R1s = slot_shift(rb, mp);
           const int C0s = slot_shift(ci, mp), C1s = slot_shift(cb, mp);
@@ -396,22 +418,22 @@ jacobi_kernel(JacBuf b, int m, int mp, const double* normA, int* counts, int* fl
           const int v = tile - nTA;
           const int R0 = (v % nVR) * JV, C0 = (v / nVR) * JC;
           const int ci = C0 + t / 16, cb = mp - 1 - ci;
-          double vu[JV / 16], vv[JV / 16];
+          T vu[JV / 16], vv[JV / 16];
 #pragma unroll
           for (int j = 0; j < JV / 16; ++j) {
             const int row = R0 + (t % 16) + 16 * j;
-            vu[j] = row < mp ? __ldcg(V + row + (int64_t)ci * mp) : 0.0;
-            vv[j] = row < mp ? __ldcg(V + row + (int64_t)cb * mp) : 0.0;
+            vu[j] = row < mp ? __ldcg(V + row + (int64_t)ci * mp) : (T)0;
+            vv[j] = row < mp ? __ldcg(V + row + (int64_t)cb * mp) : (T)0;
           }
           if (t < JC) {
             const int p = C0 + t;
-            double c, s;
+            T c, s;
             rot_from(__ldcg(Dg + p), __ldcg(Dg + mp - 1 - p), __ldcg(Od + p), thr, inv, c, s);
             rc[t] = c;
             rs[t] = s;
           }
           __syncthreads();
-          const double cc = rc[t / 16], sc = rs[t / 16];
+          const T cc = rc[t / 16], sc = rs[t / 16];
           const int c0 = slot_shift(ci, mp), c1 = slot_shift(cb, mp);
 #pragma unroll
           for (int j = 0; j < JV / 16; ++j) {
@@ -434,12 +456,12 @@ jacobi_kernel(JacBuf b, int m, int mp, const double* normA, int* counts, int* fl
   if (blockIdx.x == 0 && t == 0) {
     info[0] = sweep;                                 // sweeps run
     info[1] = cur;
-    if (!converged) atomicOr(flag, kFlagJacobiNoConv);
+    if (!converged && sizeof(T) == sizeof(double)) atomicOr(flag, kFlagJacobiNoConv);
   }
 }
 
 // lambda ascending; C[:, rank(i)] = V[0:m, i]. The layout is the identity at a sweep boundary.
-__global__ void jacobi_sort_kernel(JacBuf b, int m, int mp, const int* info, double* lambda, int* perm) {
+__global__ void jacobi_sort_kernel(JacBuf<double> b, int m, int mp, const int* info, double* lambda, int* perm) {
   const double* A = b.A[info[1]];
   // rank by the strict total order (value, index) with NaN as +inf, so perm is always a permutation
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
@@ -456,12 +478,22 @@ __global__ void jacobi_sort_kernel(JacBuf b, int m, int mp, const int* info, dou
   }
 }
 
-__global__ void jacobi_gather_kernel(JacBuf b, int m, int mp, const int* info, const int* perm, double* C) {
+__global__ void jacobi_gather_kernel(JacBuf<double> b, int m, int mp, const int* info, const int* perm, double* C) {
   const double* V = b.V[info[1]];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)m * m;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(e % m), c = (int)(e / m);
     C[e] = V[r + (int64_t)perm[c] * mp];
+  }
+}
+
+// Z (m x m, FP64) = the FP32 Jacobi eigenvectors (unsorted; the refinement orders them itself)
+__global__ void jacobi32_to_z_kernel(JacBuf<float> b, int m, int mp, const int* info, double* Z) {
+  const float* V = b.V[info[1]];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)m * m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % m), c = (int)(e / m);
+    Z[e] = (double)V[r + (int64_t)c * mp];
   }
 }
 
@@ -501,82 +533,247 @@ __global__ void eig_stats_kernel(const double* __restrict__ M, int m, double* ou
   }
 }
 
-// Refinement step, first half (Ogita and Aishima 2018, symmetric eigenvalue refinement): with R = I - Z^T Z
-// (G = Z^T Z; G = null means Z = I, R = 0) and S = Z^T M Z, lam_i = S_ii / (1 - R_ii) and the cluster radius
-// delta = 2 (||S - diag(lam)|| + ||M|| ||R||), Frobenius norms standing in for 2-norms (a larger delta only
-// treats more pairs as clustered). out: [0] delta, [1] max |E_ij| (as bits, set by the second half), [2] cluster
-// flag. One CTA.
-__global__ void refine_lam_kernel(const double* __restrict__ S, const double* __restrict__ G, int m, double nM,
-                                  double* lam, double* out) {
+// ---------------------------------------------------------------------------------- eigenvector refinement
+// One step of the symmetric eigenvector refinement of Ogita and Aishima (2018), with clustered eigenvalues solved
+// as small eigenproblems (the idea of their 2019 sequel on clustered eigenvalues). For approximate eigenvectors Z
+// (columns), G = Z^T Z, R = I - G and S = Z^T M Z:
+//   lam_i = S_ii / (1 - R_ii);
+//   for a separated pair i != j: E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i)   (the first-order correction);
+//   E_ii = R_ii / 2                                                               (first-order orthonormalisation);
+//   Z <- Z (I + E): the error of Z roughly squares.
+// S enters symmetrised, (S_ij + S_ji) / 2: then E_ij + E_ji = R_ij holds exactly, so the orthogonality of the new Z
+// does not suffer from the rounding of S divided by small eigenvalue gaps.
+// Pairs whose Ritz values are closer than max(kClusterGap x the largest coupling |S_ij + lam_j R_ij|,
+// kClusterFloor ||M||_F) would divide by a difference that the coupling or the rounding of S can dwarf. Such values
+// are grouped into clusters (runs of the sorted values with small gaps), and each cluster's block of the first-order
+// orthonormalised S, B_ab = S_ab + (lam_a + lam_b) R_ab / 2 (B_aa = lam_a), is diagonalised exactly, B = Q D Q^T,
+// by a cyclic Jacobi in shared memory. The cluster's columns of I + E are then rotated by Q (so the first-order
+// corrections from outside the cluster follow the rotated vectors). A step is accepted once every separated |E_ij|
+// is at most kRefineAccept and no cluster pair couples above the FP64 Jacobi threshold (the next error is then of
+// order kRefineAccept^2 ||M||).
+//
+// stat: [0] ||M||_F, [2] largest separated |E_ij| (as bits), [3] largest in-cluster |S_ij| (bits), [4] largest
+// coupling (bits), [5] clusters, [6] a cluster larger than kMaxCluster. Non-negative doubles order like their bit
+// patterns, so the maxima merge with integer atomics in any order.
+__device__ __forceinline__ void atomic_max_nonneg(double* p, double v) {
+  if (!(v == v)) v = CUDART_INF;                     // a NaN rejects the step
+  atomicMax(reinterpret_cast<unsigned long long*>(p), (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ double r_of(const double* G, int64_t e, int i, int j) {
+  return G ? (i == j ? 1.0 : 0.0) - G[e] : 0.0;
+}
+
+// lam_i = S_ii / G_ii (G = null: Z = I); resets the step statistics. One CTA.
+__global__ void refine_diag_kernel(const double* __restrict__ S, const double* __restrict__ G, int m, double* lam,
+                                   double* stat) {
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     const double sii = S[i + (int64_t)i * m];
     lam[i] = G ? sii / G[i + (int64_t)i * m] : sii;
   }
-  __syncthreads();
-  double a = 0.0, b = 0.0;
-  const int64_t cnt = (int64_t)m * m;
-  for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) {
-    const int i = (int)(e % m), j = (int)(e / m);
-    const double d = S[e] - (i == j ? lam[i] : 0.0);
-    a += d * d;
-    if (G) {
-      const double r = (i == j ? 1.0 : 0.0) - G[e];
-      b += r * r;
-    }
-  }
-  __shared__ double ra[1024], rb[1024];
-  ra[threadIdx.x] = a;
-  rb[threadIdx.x] = b;
-  __syncthreads();
-  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-    if ((int)threadIdx.x < off) {
-      ra[threadIdx.x] += ra[threadIdx.x + off];
-      rb[threadIdx.x] += rb[threadIdx.x + off];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    out[0] = 2.0 * (sqrt(ra[0]) + nM * sqrt(rb[0]));
-    out[1] = 0.0;
-    out[2] = 0.0;
-  }
+  if (threadIdx.x == 0)
+    for (int q = 2; q <= 6; ++q) stat[q] = 0.0;
 }
 
-// Second half: E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i) where |lam_j - lam_i| > delta, else R_ij / 2 (and a
-// pair coupled above thr there is flagged: the refinement cannot separate it); E_ii = R_ii / 2. The largest
-// |E_ij|, i != j, is merged by an atomic maximum on the bit pattern (order-independent).
-__global__ void refine_coef_kernel(const double* __restrict__ S, const double* __restrict__ G, int m,
-                                   const double* __restrict__ lam, double* stat, double thr, double* __restrict__ E) {
-  const double delta = stat[0];
-  double emax = 0.0;
-  bool clustered = false;
+// largest coupling |S_ij + lam_j R_ij|, i != j
+__global__ void refine_coupling_kernel(const double* __restrict__ S, const double* __restrict__ G, int m,
+                                       const double* __restrict__ lam, double* stat) {
+  double mx = 0.0;
   const int64_t cnt = (int64_t)m * m;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % m), j = (int)(e / m);
-    const double r = G ? (i == j ? 1.0 : 0.0) - G[e] : 0.0;
+    if (i != j) mx = fmax(mx, fabs(0.5 * (S[e] + S[j + (int64_t)i * m]) + lam[j] * r_of(G, e, i, j)));
+    else if (!(S[e] == S[e])) mx = CUDART_INF;
+  }
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(stat + 4, mx);
+}
+
+// Clusters: sort lam (strict order (value, index), NaN as +inf), cut the sorted sequence where consecutive values
+// differ by more than gap = max(kClusterGap x coupling, kClusterFloor ||M||_F), and number the runs of two or more.
+// order[r] = index of the r-th smallest; cid[i] = cluster of i or -1; cluster c = order[cls[c] .. cls[c] + cln[c]).
+// One CTA of 1024 threads; the cut positions are a bitmask in shared memory (kt <= 65535 columns).
+__global__ void __launch_bounds__(1024)
+refine_cluster_kernel(const double* __restrict__ lam, int m, double* stat, int* order, int* cid, int* cls,
+                      int* cln) {
+  __shared__ unsigned cut[2048];
+  const double coupling = stat[4];
+  const double gap = fmax(kClusterGap * coupling, kClusterFloor * stat[0]);
+  for (int w = threadIdx.x; w < 2048; w += blockDim.x) cut[w] = 0u;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double li = lam[i];
+    const double ki = isnan(li) ? CUDART_INF : li;
+    int rank = 0;
+    for (int l = 0; l < m; ++l) {
+      const double ll = lam[l];
+      const double kl = isnan(ll) ? CUDART_INF : ll;
+      rank += (kl < ki || (kl == ki && l < i)) ? 1 : 0;
+    }
+    order[rank] = i;
+    cid[i] = -1;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < m; r += blockDim.x) {
+    bool c = true;
+    if (r > 0) {
+      const double d = lam[order[r]] - lam[order[r - 1]];
+      c = !(d <= gap);                               // NaN or inf: a cut
+    }
+    if (c) atomicOr(&cut[r >> 5], 1u << (r & 31));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ncl = 0, big = 0, start = 0;
+    for (int r = 1; r <= m; ++r) {
+      if (r == m || ((cut[r >> 5] >> (r & 31)) & 1u)) {
+        const int len = r - start;
+        if (len >= 2) {
+          if (len > kMaxCluster) big = 1;
+          cls[ncl] = start;
+          cln[ncl] = len;
+          for (int q = start; q < r; ++q) cid[order[q]] = ncl;
+          ++ncl;
+        }
+        start = r;
+      }
+    }
+    stat[5] = (double)ncl;
+    stat[6] = big ? 1.0 : 0.0;
+  }
+}
+
+// E for every pair outside a cluster block; within a block E = R / 2 until the cluster solve replaces it
+__global__ void refine_coef_kernel(const double* __restrict__ S, const double* __restrict__ G, int m,
+                                   const double* __restrict__ lam, const int* __restrict__ cid, double thr,
+                                   double* stat, double* __restrict__ E) {
+  double emax = 0.0, cmax = 0.0;
+  const int64_t cnt = (int64_t)m * m;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    const double r = r_of(G, e, i, j);
+    const double sij = 0.5 * (S[e] + S[j + (int64_t)i * m]);
     double v;
     if (i == j) {
       v = 0.5 * r;
+    } else if (cid[i] >= 0 && cid[i] == cid[j]) {
+      v = 0.5 * r;
+      cmax = fmax(cmax, fabs(sij) > thr ? fabs(sij) : 0.0);
     } else {
-      const double dl = lam[j] - lam[i];
-      if (fabs(dl) > delta) {
-        v = (S[e] + lam[j] * r) / dl;
-      } else {
-        v = 0.5 * r;
-        if (fabs(S[e]) > thr) clustered = true;
-      }
+      v = (sij + lam[j] * r) / (lam[j] - lam[i]);
       emax = fmax(emax, fabs(v));
     }
     E[e] = v;
   }
-  if (!(emax == emax)) emax = CUDART_INF;    // a NaN coefficient rejects the refinement
+  if (!(emax == emax)) emax = CUDART_INF;
   for (int off = 16; off > 0; off >>= 1) {
     emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, off));
-    clustered = __any_sync(0xffffffffu, clustered);
+    cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, off));
   }
   if ((threadIdx.x & 31) == 0) {
-    atomicMax(reinterpret_cast<unsigned long long*>(stat + 1), (unsigned long long)__double_as_longlong(emax));
-    if (clustered) stat[2] = 1.0;
+    atomic_max_nonneg(stat + 2, emax);
+    atomic_max_nonneg(stat + 3, cmax);
+  }
+}
+
+// One CTA per cluster (blocks beyond the cluster count return): B = the first-order orthonormalised cluster block
+// of S, diagonalised by cyclic Jacobi with round-robin pairs (FP64, shared memory); then the cluster's columns of
+// I + E, over all m rows, are multiplied by Q.
+__global__ void __launch_bounds__(256)
+refine_cluster_eig_kernel(const double* __restrict__ S, const double* __restrict__ G, int m,
+                          const double* __restrict__ lam, const int* __restrict__ order, const int* __restrict__ cls,
+                          const int* __restrict__ cln, const double* __restrict__ stat, double* __restrict__ E) {
+  const int c = blockIdx.x;
+  if (c >= (int)stat[5] || stat[6] != 0.0) return;
+  const int start = cls[c], sz = cln[c];
+  const int sp = sz + (sz & 1);                      // padded to an even size (the pad index never rotates)
+  __shared__ double B[kMaxCluster][kMaxCluster + 1], Q[kMaxCluster][kMaxCluster + 1];
+  __shared__ double rcs[kMaxCluster / 2], rsn[kMaxCluster / 2];
+  __shared__ int ra[kMaxCluster / 2], rb[kMaxCluster / 2];
+  __shared__ int idx[kMaxCluster];
+  __shared__ double offmax;
+  const int t = threadIdx.x;
+  for (int a = t; a < sz; a += blockDim.x) idx[a] = order[start + a];
+  __syncthreads();
+  for (int e = t; e < sp * sp; e += blockDim.x) {
+    const int a = e % sp, b = e / sp;
+    double v = 0.0;
+    if (a < sz && b < sz) {
+      const int i = idx[a], j = idx[b];
+      if (a == b) {
+        v = lam[i];
+      } else {
+        const int64_t eij = i + (int64_t)j * m, eji = j + (int64_t)i * m;
+        v = 0.5 * (S[eij] + S[eji]) + 0.5 * (lam[i] + lam[j]) * r_of(G, eij, i, j);
+      }
+    }
+    B[a][b] = v;
+    Q[a][b] = (a == b) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int np = sp / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (t == 0) offmax = 0.0;
+    __syncthreads();
+    double om = 0.0;
+    for (int e = t; e < sp * sp; e += blockDim.x) {
+      const int a = e % sp, b = e / sp;
+      if (a != b) om = fmax(om, fabs(B[a][b]));
+    }
+    for (int off = 16; off > 0; off >>= 1) om = fmax(om, __shfl_xor_sync(0xffffffffu, om, off));
+    if ((t & 31) == 0) atomic_max_nonneg(&offmax, om);
+    __syncthreads();
+    double scale = 0.0;
+    for (int a = 0; a < sz; ++a) scale = fmax(scale, fabs(B[a][a]));
+    if (!(offmax > 1e-17 * scale) || !(offmax == offmax)) break;
+    for (int r = 0; r < sp - 1; ++r) {
+      if (t < np) {
+        // circle method: element 0 fixed, the others rotate by r
+        const int pa = t == 0 ? 0 : ((t - 1 + r) % (sp - 1)) + 1;
+        const int pb = ((sp - 1 - t - 1 + r) % (sp - 1)) + 1;
+        const int a = pa < pb ? pa : pb, b = pa < pb ? pb : pa;
+        double cs = 1.0, sn = 0.0;
+        const double apq = B[a][b];
+        if (b < sz && apq != 0.0) {
+          const double th = (B[b][b] - B[a][a]) / (2.0 * apq);
+          double tt = 1.0 / (fabs(th) + sqrt(th * th + 1.0));
+          if (th < 0.0) tt = -tt;
+          cs = 1.0 / sqrt(tt * tt + 1.0);
+          sn = tt * cs;
+        }
+        ra[t] = a; rb[t] = b; rcs[t] = cs; rsn[t] = sn;
+      }
+      __syncthreads();
+      for (int e = t; e < np * sp; e += blockDim.x) {          // rows: B <- J^T B
+        const int q = e % np, j = e / np;
+        const int a = ra[q], b = rb[q];
+        const double x = B[a][j], y = B[b][j];
+        B[a][j] = rcs[q] * x - rsn[q] * y;
+        B[b][j] = rsn[q] * x + rcs[q] * y;
+      }
+      __syncthreads();
+      for (int e = t; e < np * sp; e += blockDim.x) {          // columns: B <- B J, Q <- Q J
+        const int q = e % np, i = e / np;
+        const int a = ra[q], b = rb[q];
+        const double x = B[i][a], y = B[i][b];
+        B[i][a] = rcs[q] * x - rsn[q] * y;
+        B[i][b] = rsn[q] * x + rcs[q] * y;
+        const double u = Q[i][a], w = Q[i][b];
+        Q[i][a] = rcs[q] * u - rsn[q] * w;
+        Q[i][b] = rsn[q] * u + rcs[q] * w;
+      }
+      __syncthreads();
+    }
+  }
+  // F = I + E restricted to the cluster's columns, F <- F Q, row by row (each thread owns whole rows)
+  for (int i = t; i < m; i += blockDim.x) {
+    double f[kMaxCluster];
+#pragma unroll 4
+    for (int a = 0; a < sz; ++a) f[a] = E[i + (int64_t)idx[a] * m] + (i == idx[a] ? 1.0 : 0.0);
+    for (int b = 0; b < sz; ++b) {
+      double acc = 0.0;
+      for (int a = 0; a < sz; ++a) acc = fma(f[a], Q[a][b], acc);
+      E[i + (int64_t)idx[b] * m] = acc - (i == idx[b] ? 1.0 : 0.0);
+    }
   }
 }
 
@@ -643,7 +840,7 @@ inline unsigned grid_for(int64_t cnt) {
 }
 
 struct CoopLimit {
-  int chol = 0, jac = 0;
+  int chol = 0, jac = 0, jac32 = 0;
 };
 
 const CoopLimit& coop_limits() {
@@ -656,8 +853,11 @@ const CoopLimit& coop_limits() {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, chol_inv_kernel, 256, 0);
     l.chol = (per > 0 ? per : 1) * sms;
     per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, jacobi_kernel, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, jacobi_kernel<double>, 256, 0);
     l.jac = (per > 0 ? per : 1) * sms;
+    per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, jacobi_kernel<float>, 256, 0);
+    l.jac32 = (per > 0 ? per : 1) * sms;
     return l;
   }();
   return lim;
@@ -696,7 +896,103 @@ cudaError_t coop_launch(const void* fn, unsigned grid, void** args, cudaStream_t
 inline int pad_tile(int m) { return (int)ceil_div(m, TB) * TB; }
 inline int pad_jac(int m) { return (int)ceil_div(m < 2 ? 2 : m, 32) * 32; }
 
+// Eigensolver workspace (jacobi_ws_elems doubles). The refinement uses Z, E, T, S, lam, stat and the integer
+// arrays; the FP64 Jacobi reuses Z..S as its matrix and vector ping-pong buffers and lam as its diagonal/pair
+// arrays; the FP32 Jacobi keeps its buffers in T, S and lam, which the refinement only fills after reading Z.
+struct EigWs {
+  int mp;
+  double *Z, *E, *T, *S, *lam, *stat;
+  int *counts, *perm, *order, *cid, *cls, *cln;
+};
+
+EigWs eig_ws(double* ws, int m) {
+  EigWs w;
+  w.mp = pad_jac(m);
+  const size_t sq = (size_t)w.mp * w.mp;
+  w.Z = ws;
+  w.E = ws + sq;
+  w.T = ws + 2 * sq;
+  w.S = ws + 3 * sq;
+  w.lam = ws + 4 * sq;
+  w.stat = w.lam + 4 * (size_t)w.mp;
+  w.counts = reinterpret_cast<int*>(w.stat + 16);
+  w.perm = w.counts + kJacobiMaxSweeps + 8;
+  w.order = w.perm + w.mp;
+  w.cid = w.order + w.mp;
+  w.cls = w.cid + w.mp;
+  w.cln = w.cls + w.mp;
+  return w;
+}
+
+template <typename T>
+JacBuf<T> jac_buffers(const EigWs& w) {
+  JacBuf<T> jb;
+  const size_t sq = (size_t)w.mp * w.mp;
+  if (sizeof(T) == sizeof(double)) {
+    T* p = reinterpret_cast<T*>(w.Z);
+    for (int i = 0; i < 2; ++i) { jb.A[i] = p; p += sq; }
+    for (int i = 0; i < 2; ++i) { jb.V[i] = p; p += sq; }
+  } else {
+    T* p = reinterpret_cast<T*>(w.T);                // 4 mp^2 floats in the 2 mp^2 doubles of T and S
+    for (int i = 0; i < 2; ++i) { jb.A[i] = p; p += sq; }
+    for (int i = 0; i < 2; ++i) { jb.V[i] = p; p += sq; }
+  }
+  T* d = reinterpret_cast<T*>(w.lam);
+  for (int i = 0; i < 2; ++i) { jb.Dg[i] = d; d += w.mp; }
+  for (int i = 0; i < 2; ++i) { jb.Od[i] = d; d += w.mp; }
+  return jb;
+}
+
+// Runs the Jacobi kernel of precision T on M (m x m, upper triangle read) into the buffers of w; info receives the
+// sweep count and the buffer holding the result.
+template <typename T>
+cudaError_t run_jacobi(const double* M, int m, const EigWs& w, const JacBuf<T>& jb, double tol, int max_sweeps,
+                       int* flag, unsigned* bar, int* info, cudaStream_t s) {
+  const int mp = w.mp;
+  double* nrm = w.stat + 8;
+  cudaError_t e = cudaMemsetAsync(bar, 0, barrier_words() * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(w.counts, 0, sizeof(int) * kJacobiMaxSweeps, s);
+  if (e != cudaSuccess) return e;
+  const int64_t cnt = (int64_t)mp * mp;
+  jacobi_init_kernel<T><<<grid_for(cnt), 256, 0, s>>>(M, m, mp, jb.A[0], jb.V[0], jb.Dg[0], jb.Od[0]);
+  count_launch();
+  frob_kernel<T><<<1, 1024, 0, s>>>(jb.A[0], cnt, nrm);
+  count_launch();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int P = mp / 2;
+  const int64_t want = (int64_t)(P / JR) * (P / JR) + ceil_div(mp, JV) * (P / JC);
+  const int lim = sizeof(T) == sizeof(double) ? coop_limits().jac : coop_limits().jac32;
+  const int grid = (int)(want < lim ? (want < 1 ? 1 : want) : lim);
+  const double* nrm_c = nrm;
+  JacBuf<T> b = jb;
+  void* args[] = {(void*)&b, (void*)&m, (void*)&mp, (void*)&nrm_c, (void*)&tol, (void*)&max_sweeps,
+                  (void*)&w.counts, (void*)&flag, (void*)&bar, (void*)&info};
+  count_launch();
+  return coop_launch((const void*)jacobi_kernel<T>, (unsigned)grid, args, s);
+}
+
+// Every CTA but the last waits at one grid barrier that the last CTA never reaches, so the wait cannot complete:
+// the bounded spin gives up after spin_limit polls, sets kFlagTimeout and every waiting CTA returns.
+__global__ void __launch_bounds__(256) barrier_probe_kernel(unsigned* bar, int* flag, long long spin_limit) {
+  unsigned gen = 0;
+  if (blockIdx.x == gridDim.x - 1) return;
+  grid_sync(bar, gridDim.x, flag, gen, spin_limit);
+}
+
 }  // namespace
+
+cudaError_t barrier_timeout_probe(long long spin_limit, int* flag, unsigned* bar, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(bar, 0, barrier_words() * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  int grid = coop_limits().chol;
+  if (grid > 64) grid = 64;
+  if (grid < 2) grid = 2;
+  void* args[] = {(void*)&bar, (void*)&flag, (void*)&spin_limit};
+  count_launch();
+  return coop_launch((const void*)barrier_probe_kernel, (unsigned)grid, args, s);
+}
 
 size_t barrier_words() { return 2; }
 
@@ -728,49 +1024,20 @@ cudaError_t chol_inv(const double* G, int m, double shift, double* Rinv, double*
 
 size_t jacobi_ws_elems(int m) {
   const size_t mp = (size_t)pad_jac(m);
-  return 4 * mp * mp + 4 * mp + 8 + (size_t)kJacobiMaxSweeps + mp + 8;
+  return 4 * mp * mp + 4 * mp + 16 + ceil_div((int64_t)kJacobiMaxSweeps + 8 + 5 * (int64_t)mp, 2) + 8;
 }
 
 cudaError_t jacobi_eigh(const double* M, int m, double* lambda, double* C, double* ws, int* flag, unsigned* bar,
                         int* sweeps_out_dev, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
-  const int mp = pad_jac(m);
-  JacBuf jb;
-  double* p = ws;
-  for (int i = 0; i < 2; ++i) { jb.A[i] = p; p += (size_t)mp * mp; }
-  for (int i = 0; i < 2; ++i) { jb.V[i] = p; p += (size_t)mp * mp; }
-  for (int i = 0; i < 2; ++i) { jb.Dg[i] = p; p += mp; }
-  for (int i = 0; i < 2; ++i) { jb.Od[i] = p; p += mp; }
-  double* nrm = p;
-  int* counts = reinterpret_cast<int*>(nrm + 8);
-  int* perm = counts + kJacobiMaxSweeps + 8;
+  const EigWs w = eig_ws(ws, m);
+  const JacBuf<double> jb = jac_buffers<double>(w);
   int* info = sweeps_out_dev;
-  cudaError_t e = cudaMemsetAsync(bar, 0, barrier_words() * sizeof(unsigned), s);
+  cudaError_t e = run_jacobi<double>(M, m, w, jb, kJacobiTol, kJacobiMaxSweeps, flag, bar, info, s);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(counts, 0, sizeof(int) * kJacobiMaxSweeps, s);
-  if (e != cudaSuccess) return e;
-  const int64_t cnt = (int64_t)mp * mp;
-  jacobi_init_kernel<<<(unsigned)(ceil_div(cnt, 256) < 4096 ? ceil_div(cnt, 256) : 4096), 256, 0, s>>>(
-      M, m, mp, jb.A[0], jb.V[0], jb.Dg[0], jb.Od[0]);
+  jacobi_sort_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(jb, m, w.mp, info, lambda, w.perm);
   count_launch();
-  frob_kernel<<<1, 1024, 0, s>>>(jb.A[0], cnt, nrm);
-  count_launch();
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const int P = mp / 2;
-  const int64_t want = (int64_t)(P / JR) * (P / JR) + ceil_div(mp, JV) * (P / JC);
-  const int lim = coop_limits().jac;
-  const int grid = (int)(want < lim ? (want < 1 ? 1 : want) : lim);
-  const double* nrm_c = nrm;
-  void* args[] = {(void*)&jb, (void*)&m, (void*)&mp, (void*)&nrm_c, (void*)&counts, (void*)&flag, (void*)&bar,
-                  (void*)&info};
-  count_launch();
-  e = coop_launch((const void*)jacobi_kernel, (unsigned)grid, args, s);
-  if (e != cudaSuccess) return e;
-  jacobi_sort_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(jb, m, mp, info, lambda, perm);
-  count_launch();
-  jacobi_gather_kernel<<<(unsigned)(ceil_div((int64_t)m * m, 256) < 4096 ? ceil_div((int64_t)m * m, 256) : 4096), 256,
-                         0, s>>>(jb, m, mp, info, perm, C);
+  jacobi_gather_kernel<<<grid_for((int64_t)m * m), 256, 0, s>>>(jb, m, w.mp, info, w.perm, C);
   count_launch();
   return cudaGetLastError();
 }
@@ -779,82 +1046,88 @@ cudaError_t jacobi_eigh(const double* M, int m, double* lambda, double* C, doubl
 // in a solve is nearly diagonal in the basis of the previous Ritz vectors, and then the parallel Jacobi method still
 // pays its full rounds of grid barriers. (1) If no off-diagonal entry exceeds kJacobiTol ||M||_F (the Jacobi stop
 // test), the eigenpairs are the sorted diagonal and unit vectors. (2) If none exceeds kRefineTau ||M||_F, the
-// eigenvectors are refined from the identity by the iteration of Ogita and Aishima (2018): each step is a few
-// m x m FP64 products, and the error roughly squares. A step whose largest coefficient |E_ij| is at most
-// kRefineAccept, with no pair left clustered above the threshold, is accepted: the remaining error of Z is of order
-// kRefineAccept^2, and the eigenvalues are the Rayleigh quotients of the final vectors. (3) Otherwise, or when
-// kRefineSteps steps do not get there, parallel Jacobi on M. path_out: 0 Jacobi, 1 diagonal, 2 refined.
+// eigenvectors are refined from the identity (see the refinement kernels above). (3) Otherwise a single-precision
+// Jacobi, whose rotations run on the wide FP32 pipe, gives eigenvectors accurate to about 1e-6, and the refinement
+// takes them to FP64 accuracy in two or three steps of m x m products. (4) If a refinement does not settle within
+// kRefineSteps steps, or a cluster exceeds kMaxCluster values, FP64 Jacobi on M. Accepted refinements take the
+// Rayleigh quotients of the final vectors as eigenvalues.
 // msym: m x m scratch (not aliasing M or C) for the symmetrised M.
 cudaError_t dense_eigh_auto(const double* Min, int m, double* lambda, double* C, double* ws, double* msym,
-                            double* part, size_t part_cap, int* flag, unsigned* bar, int* sweeps_out_dev,
-                            int* path_out, cudaStream_t s) {
+                            const KxK& g, int* flag, unsigned* bar, int* sweeps_out_dev, int* path_out,
+                            cudaStream_t s) {
   *path_out = 0;
   if (m <= 0) return cudaSuccess;
-  const int mp = pad_jac(m);
-  const size_t sq = (size_t)mp * mp;
-  double* Z = ws;
-  double* E = ws + sq;
-  double* T = ws + 2 * sq;
-  double* S = ws + 3 * sq;
-  double* lamw = ws + 4 * sq;                 // the Jacobi diagonal/pair arrays (4 mp doubles)
-  double* stat = lamw + 4 * (size_t)mp;       // the Jacobi norm slot (8 doubles)
-  int* perm = reinterpret_cast<int*>(stat + 8) + kJacobiMaxSweeps + 8;
+  const EigWs w = eig_ws(ws, m);
   double* G = C;                              // Z^T Z lives in the output until the final gather
   const double* M = msym;
   symmetrize_kernel<<<grid_for((int64_t)m * m), 256, 0, s>>>(Min, m, msym);
   count_launch();
   cudaError_t e;
-  eig_stats_kernel<<<1, 1024, 0, s>>>(M, m, stat);
+  eig_stats_kernel<<<1, 1024, 0, s>>>(M, m, w.stat);
   count_launch();
-  double h[3] = {0.0, 0.0, 0.0};
-  if ((e = cudaMemcpyAsync(h, stat, 2 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+  double h[8] = {};
+  if ((e = cudaMemcpyAsync(h, w.stat, 2 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
   const double nM = h[0], off = h[1], thr = kJacobiTol * nM;
-  if (std::isfinite(nM) && off <= thr) {
-    rank_sort_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(M, (int64_t)m + 1, m, lambda, perm);
+  if (!std::isfinite(nM)) return jacobi_eigh(Min, m, lambda, C, ws, flag, bar, sweeps_out_dev, s);
+  if (off <= thr) {
+    rank_sort_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(M, (int64_t)m + 1, m, lambda, w.perm);
     count_launch();
-    gather_perm_kernel<<<grid_for((int64_t)m * m), 256, 0, s>>>(nullptr, m, perm, C);
+    gather_perm_kernel<<<grid_for((int64_t)m * m), 256, 0, s>>>(nullptr, m, w.perm, C);
     count_launch();
     *path_out = 1;
     return cudaGetLastError();
   }
-  if (std::isfinite(nM) && off <= kRefineTau * nM) {
-    const int64_t cnt = (int64_t)m * m;
-    for (int t = 0; t < kRefineSteps; ++t) {
-      const double* St = M;
-      const double* Gt = nullptr;
-      if (t > 0) {
-        if ((e = small_gemm(true, Z, m, Z, m, m, m, m, G, m, part, part_cap, s)) != cudaSuccess) return e;
-        if ((e = small_gemm(false, M, m, Z, m, m, m, m, T, m, part, part_cap, s)) != cudaSuccess) return e;
-        if ((e = small_gemm(true, Z, m, T, m, m, m, m, S, m, part, part_cap, s)) != cudaSuccess) return e;
-        St = S;
-        Gt = G;
-      }
-      refine_lam_kernel<<<1, 1024, 0, s>>>(St, Gt, m, nM, lamw, stat);
+  const bool from_identity = off <= kRefineTau * nM;
+  if (!from_identity) {
+    // single-precision Jacobi for the starting vectors
+    const JacBuf<float> jb = jac_buffers<float>(w);
+    e = run_jacobi<float>(M, m, w, jb, kJacobiTol32, kJacobiMaxSweeps32, flag, bar, sweeps_out_dev, s);
+    if (e != cudaSuccess) return e;
+    jacobi32_to_z_kernel<<<grid_for((int64_t)m * m), 256, 0, s>>>(jb, m, w.mp, sweeps_out_dev, w.Z);
+    count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const int64_t cnt = (int64_t)m * m;
+  const unsigned gcl = (unsigned)ceil_div(m, 2);
+  for (int t = 0; t < kRefineSteps; ++t) {
+    const double* St = M;
+    const double* Gt = nullptr;
+    if (t > 0 || !from_identity) {
+      if ((e = kxk_gemm(g, true, w.Z, m, w.Z, m, m, m, m, G, m, s)) != cudaSuccess) return e;        // Z^T Z
+      if ((e = kxk_gemm(g, true, M, m, w.Z, m, m, m, m, w.T, m, s)) != cudaSuccess) return e;        // M Z
+      if ((e = kxk_gemm(g, true, w.Z, m, w.T, m, m, m, m, w.S, m, s)) != cudaSuccess) return e;      // Z^T M Z
+      St = w.S;
+      Gt = G;
+    }
+    refine_diag_kernel<<<1, 1024, 0, s>>>(St, Gt, m, w.lam, w.stat);
+    refine_coupling_kernel<<<grid_for(cnt), 256, 0, s>>>(St, Gt, m, w.lam, w.stat);
+    refine_cluster_kernel<<<1, 1024, 0, s>>>(w.lam, m, w.stat, w.order, w.cid, w.cls, w.cln);
+    refine_coef_kernel<<<grid_for(cnt), 256, 0, s>>>(St, Gt, m, w.lam, w.cid, thr, w.stat, w.E);
+    refine_cluster_eig_kernel<<<gcl, 256, 0, s>>>(St, Gt, m, w.lam, w.order, w.cls, w.cln, w.stat, w.E);
+    count_launch(5);
+    if (t == 0 && from_identity) {
+      identity_plus_kernel<<<grid_for(cnt), 256, 0, s>>>(w.E, m, w.Z);
       count_launch();
-      refine_coef_kernel<<<grid_for(cnt), 256, 0, s>>>(St, Gt, m, lamw, stat, thr, E);
+    } else {
+      if ((e = kxk_gemm(g, false, w.Z, m, w.E, m, m, m, m, w.T, m, s)) != cudaSuccess) return e;     // Z E
+      add_kernel<<<grid_for(cnt), 256, 0, s>>>(w.T, cnt, w.Z);
       count_launch();
-      if (t == 0) {
-        identity_plus_kernel<<<grid_for(cnt), 256, 0, s>>>(E, m, Z);
-        count_launch();
-      } else {
-        if ((e = small_gemm(false, Z, m, E, m, m, m, m, T, m, part, part_cap, s)) != cudaSuccess) return e;
-        add_kernel<<<grid_for(cnt), 256, 0, s>>>(T, cnt, Z);
-        count_launch();
-      }
-      if ((e = cudaMemcpyAsync(h, stat, 3 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
-      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-      if (h[1] <= kRefineAccept && h[2] == 0.0) {
-        if ((e = small_gemm(false, M, m, Z, m, m, m, m, T, m, part, part_cap, s)) != cudaSuccess) return e;
-        rayleigh_quotient_kernel<<<(unsigned)ceil_div(m, 8), 256, 0, s>>>(Z, T, m, lamw);
-        count_launch();
-        rank_sort_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(lamw, 1, m, lambda, perm);
-        count_launch();
-        gather_perm_kernel<<<grid_for(cnt), 256, 0, s>>>(Z, m, perm, C);
-        count_launch();
-        *path_out = 2;
-        return cudaGetLastError();
-      }
+    }
+    if ((e = cudaMemcpyAsync(h + 2, w.stat + 2, 5 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    if (h[6] != 0.0) break;                                   // a cluster too large for shared memory
+    if (h[2] <= kRefineAccept && h[3] <= thr) {
+      if ((e = kxk_gemm(g, true, M, m, w.Z, m, m, m, m, w.T, m, s)) != cudaSuccess) return e;        // M Z
+      rayleigh_quotient_kernel<<<(unsigned)ceil_div(m, 8), 256, 0, s>>>(w.Z, w.T, m, w.lam);
+      count_launch();
+      rank_sort_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(w.lam, 1, m, lambda, w.perm);
+      count_launch();
+      gather_perm_kernel<<<grid_for(cnt), 256, 0, s>>>(w.Z, m, w.perm, C);
+      count_launch();
+      *path_out = from_identity ? 2 : 3;
+      return cudaGetLastError();
     }
   }
   return jacobi_eigh(Min, m, lambda, C, ws, flag, bar, sweeps_out_dev, s);

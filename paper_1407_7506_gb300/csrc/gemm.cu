@@ -306,6 +306,21 @@ cudaError_t small_gemm(bool trans_a, const double* A, int64_t lda, const double*
   return gram_reduce_partials(part, nsplit, m, p, C, ldc, false, s);
 }
 
+cudaError_t kxk_gemm(const KxK& g, bool trans_a, const double* A, int64_t lda, const double* B, int64_t ldb, int m,
+                     int p, int kdim, double* C, int ldc, cudaStream_t s) {
+  if (m <= 0 || p <= 0) return cudaSuccess;
+  // the emulation needs a 128 x 64 output tile grid and a reduction long enough to amortise its exponent and
+  // slicing passes; smaller products stay on the FP64 pipe
+  const bool tc = g.ozaki && m >= 128 && p >= 128 && kdim >= 128;
+  if (!tc) return small_gemm(trans_a, A, lda, B, ldb, m, p, kdim, C, ldc, g.part, g.part_cap, s);
+  if (trans_a) {
+    const bool sym = (A == B && lda == ldb && m == p);
+    return oz_gram(A, lda, B, ldb, kdim, m, p, C, ldc, sym, g.part, g.part_cap, g.exps, g.img, g.img_bytes, g.flag,
+                   s);
+  }
+  return oz_update(A, lda, B, (int)ldb, m, kdim, p, C, ldc, Epi::Store, g.exps, g.img, g.img_bytes, g.flag, s);
+}
+
 cudaError_t gemm_nn(const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p, double* Y,
                     int64_t ldy, const double* Yin, int64_t ldyin, Epi epi, bool g_upper, const ResidualArgs* ra,
                     cudaStream_t s) {

@@ -16,9 +16,18 @@ constexpr double kJacobiTol = 1e-14;    // k x k Jacobi: rotate while |a_pq| > k
                                         // left below that adds < ~1e-12 to a Ritz residual (tol is 1e-8)
 constexpr double kJacobiTolSmall = 1e-16;  // sub-block warp Jacobi
 constexpr int kJacobiMaxSweeps = 60;
-constexpr double kRefineTau = 1e-6;      // try eigenvector refinement when max |M_ij| (i != j) <= kRefineTau ||M||_F
+constexpr double kRefineTau = 1e-6;      // refine from the identity when max |M_ij| (i != j) <= kRefineTau ||M||_F
 constexpr int kRefineSteps = 4;          // refinement steps before falling back to Jacobi
 constexpr double kRefineAccept = 1e-8;   // accept a refinement step whose largest |E_ij| (i != j) is at most this
+constexpr double kJacobiTol32 = 3e-7;    // single-precision Jacobi (start of the refinement): rotate while
+                                         // |a_pq| > kJacobiTol32 ||A||_F
+constexpr int kJacobiMaxSweeps32 = 16;
+constexpr double kClusterGap = 4.0;      // refinement: eigenvalues closer than kClusterGap x the largest coupling
+                                         // |S_ij + lam_j R_ij| form a cluster, solved as one small eigenproblem
+constexpr double kClusterFloor = 1e-7;   // ... and always those closer than kClusterFloor ||M||_F: there rounding in
+                                         // S (~1e-16 ||M|| sqrt(m)) would give first-order coefficients above
+                                         // kRefineAccept although the pair's vectors are determined only up to it
+constexpr int kMaxCluster = 48;          // largest cluster solved in shared memory (beyond it: FP64 Jacobi)
 constexpr int kPolarMaxTerms = 8;        // most series terms of the polar orthonormalisation
 constexpr int kMaxSbsize = 16;          // 3q <= 48 fits the warp-level sub-block solver
 
@@ -122,6 +131,9 @@ cudaError_t realform_to_cplx(const double* Y, int64_t ldy, int64_t n, int k, dou
 cudaError_t density_c(const double* Z, int64_t ldz, int64_t n, int k, double scale, double* rho, cudaStream_t s);
 // Polar orthonormalisation helpers (m x m, leading dimension m): Y = G - I in place with fro2[0] = ||Y||_F^2;
 // Z = a Y + b I; Z += b I.
+// Rayleigh-Ritz Grams with kl locked leading columns: G[0:kl, 0:kl] = I, M[0:kl, 0:kl] = diag(lam_lock), and the
+// lower-left blocks G[kl:, 0:kl], M[kl:, 0:kl] mirrored from the computed upper-right ones (m x m, ld m).
+cudaError_t locked_gram_fill(double* G, double* M, int m, int kl, const double* lam_lock, cudaStream_t s);
 cudaError_t eye_residual(double* G, int m, double* fro2, cudaStream_t s);
 cudaError_t scaled_plus_identity(const double* Y, int m, double a, double b, double* Z, cudaStream_t s);
 cudaError_t add_diag(double* Z, int m, double b, cudaStream_t s);
@@ -140,6 +152,23 @@ cudaError_t block_update(double* X, const double* W, double* P, int64_t ld, int6
                          int has_p, const double* coef, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------------------- dense k x k
+// How the dense k x k products of the Rayleigh-Ritz step (reduction, back-transformation, eigenvector refinement)
+// and of the polar series run: FP64 split-K products on the FMA pipe, or, when ozaki is set and the product is
+// large enough to fill the GPU, the FP64-accurate Ozaki emulation on the BF16 tensor cores.
+struct KxK {
+  double* part;         // split partials (>= m * p doubles)
+  size_t part_cap;
+  bool ozaki;
+  int* exps;            // Ozaki exponent workspace (oz_exp_elems of the largest operand)
+  uint8_t* img;         // Ozaki digit images (may be NULL)
+  size_t img_bytes;
+  int* flag;            // tensor-core timeout flag
+};
+// C (m x p, ldc) = op(A) B: op(A) = A^T with A kdim x m when trans_a, else A with A m x kdim; B is kdim x p.
+// C must not overlap A or B. With trans_a and A == B (m == p) the result is exactly symmetric.
+cudaError_t kxk_gemm(const KxK& g, bool trans_a, const double* A, int64_t lda, const double* B, int64_t ldb, int m,
+                     int p, int kdim, double* C, int ldc, cudaStream_t s);
+
 size_t chol_ws_elems(int m);
 // Rinv (m x m, ldr = m, upper) = R^{-1} for G + shift I = R^T R (G m x m, ldg = m). Sets kFlagCholBreakdown in
 // *flag on a relative pivot below kCholPivotTol.
@@ -149,12 +178,17 @@ size_t jacobi_ws_elems(int m);
 // lambda ascending (m), C (m x m) eigenvectors of symmetric M (m x m, upper read).
 cudaError_t jacobi_eigh(const double* M, int m, double* lambda, double* C, double* ws, int* flag, unsigned* bar,
                         int* sweeps_out_dev, cudaStream_t s);
-// The same decomposition, cheapest route first: diagonal M, eigenvector refinement of a nearly diagonal M, else
-// jacobi_eigh. ws: jacobi_ws_elems(m); msym: m x m scratch; part: small_gemm partials (>= m * m). Synchronises
-// the stream. path_out: 0 Jacobi, 1 diagonal, 2 refined.
+// The same decomposition, cheapest route first: a diagonal M is sorted; a nearly diagonal M has its eigenvectors
+// refined from the identity; otherwise a single-precision Jacobi gives the start of the refinement; FP64 Jacobi
+// (jacobi_eigh) is the fallback. ws: jacobi_ws_elems(m); msym: m x m scratch; g: how the m x m products run.
+// Synchronises the stream. path_out: 0 FP64 Jacobi, 1 diagonal, 2 refined from the identity, 3 refined from the
+// single-precision Jacobi.
 cudaError_t dense_eigh_auto(const double* M, int m, double* lambda, double* C, double* ws, double* msym,
-                            double* part, size_t part_cap, int* flag, unsigned* bar, int* sweeps_out_dev,
-                            int* path_out, cudaStream_t s);
+                            const KxK& g, int* flag, unsigned* bar, int* sweeps_out_dev, int* path_out,
+                            cudaStream_t s);
 size_t barrier_words();
+// Runs a cooperative kernel whose grid barrier can never complete (one CTA never arrives) with the given bound on
+// the wait: the waiting CTAs give up, set kFlagTimeout in *flag and return.
+cudaError_t barrier_timeout_probe(long long spin_limit, int* flag, unsigned* bar, cudaStream_t s);
 
 }  // namespace ppcg

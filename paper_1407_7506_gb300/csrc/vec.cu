@@ -258,6 +258,32 @@ __global__ void add_diag_kernel(double* Z, int m, double b) {
 
 int64_t norm_row_tiles(int64_t n) { return ceil_div(n, kRows); }
 
+// Rayleigh-Ritz Grams with kl leading locked columns (m x m, leading dimension m, columns kl.. computed): the
+// locked block becomes I (G) and diag(lam_lock) (M), and the lower-left blocks mirror the computed upper-right ones.
+__global__ void locked_gram_fill_kernel(double* G, double* M, int m, int kl, const double* __restrict__ lam_lock) {
+  const int64_t cnt = (int64_t)kl * m;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % m), j = (int)(e / m);      // column j < kl
+    const int64_t o = i + (int64_t)j * m;
+    if (i < kl) {
+      G[o] = (i == j) ? 1.0 : 0.0;
+      M[o] = (i == j) ? lam_lock[i] : 0.0;
+    } else {
+      G[o] = G[j + (int64_t)i * m];
+      M[o] = M[j + (int64_t)i * m];
+    }
+  }
+}
+
+cudaError_t locked_gram_fill(double* G, double* M, int m, int kl, const double* lam_lock, cudaStream_t s) {
+  if (kl <= 0) return cudaSuccess;
+  const int64_t cnt = (int64_t)kl * m;
+  const int64_t b = ceil_div(cnt, 256);
+  locked_gram_fill_kernel<<<(unsigned)(b < 4096 ? b : 4096), 256, 0, s>>>(G, M, m, kl, lam_lock);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t eye_residual(double* G, int m, double* fro2, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
   eye_residual_kernel<<<1, 1024, 0, s>>>(G, m, fro2);

@@ -29,7 +29,7 @@ def _declared():
 
 def test_exports_match_headers(lib):
     declared = _declared()
-    assert len(declared) == 18
+    assert len(declared) == 19
     assert sorted(declared) == sorted(pk.EXPORTS)
     out = subprocess.run(["nm", "-D", "--defined-only", pk.LIB_PATH], capture_output=True, text=True).stdout
     exported = set(re.findall(r"\bT (ppcg_\w+)", out))

@@ -202,6 +202,53 @@ def test_dense_eigh_diagonal_and_cluster():
     np.testing.assert_allclose(M @ C, C * got_l, atol=1e-14)
 
 
+def _eigh_case(kind, m, rng):
+    """Symmetric test matrices of the shapes a Rayleigh-Ritz step meets: a random spectrum, clusters of ten values
+    10^-12 apart, exact multiplicity 8, and a nearly diagonal matrix (off-diagonal 1e-3)."""
+    if kind == "neardiag":
+        B = rng.standard_normal((m, m))
+        return np.diag(np.sort(rng.standard_normal(m)) * 10) + 1e-3 * (B + B.T)
+    Q = np.linalg.qr(rng.standard_normal((m, m)))[0]
+    if kind == "random":
+        lam = rng.standard_normal(m)
+    elif kind == "clustered":
+        lam = np.concatenate([rng.standard_normal(m - 60), np.repeat(rng.standard_normal(6), 10) +
+                              1e-12 * rng.standard_normal(60)])
+    else:                                            # "degenerate"
+        lam = np.repeat(rng.standard_normal(m // 8), 8)
+    M = (Q * lam) @ Q.T
+    return 0.5 * (M + M.T)
+
+
+@pytest.mark.parametrize("fp64_gemm", [0, 1])
+@pytest.mark.parametrize("kind", ["random", "clustered", "degenerate", "neardiag"])
+@pytest.mark.parametrize("m", [512, 1024])
+def test_dense_eigh_large(m, kind, fp64_gemm):
+    # the k x k eigensolve at the sizes of the 48^3, k = 1024 workload: the single-precision Jacobi start and the
+    # FP64 refinement with cluster solves (m x m products on the FP64 pipe, or on the tensor cores when the handle
+    # emulates its FP64 GEMMs), against LAPACK
+    rng = _rng(m + len(kind))
+    M = _eigh_case(kind, m, rng)
+    with Handle(np.zeros(16 ** 3), 16, kt=m, sbsize=1, fp64_gemm=fp64_gemm) as H:
+        Md = dev(M)
+        ld = torch.empty(m, dtype=torch.float64, device="cuda")
+        Cd = torch.empty((m, m), dtype=torch.float64, device="cuda")
+        pk.ppcg_dense_eigh(H.h, ptr(Md), m, ptr(ld), ptr(Cd))
+        got_l, C = ld.cpu().numpy(), host(Cd)
+    ref_l = np.linalg.eigvalsh(M)
+    nrm = np.linalg.norm(M)
+    np.testing.assert_allclose(got_l, ref_l, rtol=0, atol=1e-13 * nrm)
+    np.testing.assert_allclose(C.T @ C, np.eye(m), atol=1e-12)
+    np.testing.assert_allclose(M @ C, C * got_l, atol=1e-12 * nrm)
+    if kind == "degenerate":                          # 8-fold eigenspaces against LAPACK's projectors
+        _, U = np.linalg.eigh(M)
+        vals = ref_l[::8]
+        for g in range(0, m // 8, 16):
+            gap = np.min(np.abs(np.delete(vals, g) - vals[g]))
+            P1, P2 = C[:, 8 * g:8 * g + 8] @ C[:, 8 * g:8 * g + 8].T, U[:, 8 * g:8 * g + 8] @ U[:, 8 * g:8 * g + 8].T
+            assert np.linalg.norm(P1 - P2, 2) <= 1e-13 * nrm / gap
+
+
 def test_dense_eigh_tiny_and_repeated_diagonal():
     # m = 1 and m = 2 (diagonal, nearly diagonal, dense) and a diagonal with repeated values: equal eigenvalues
     # keep their index order, so the eigenvectors are the unit vectors in a stable sort of the diagonal

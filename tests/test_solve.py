@@ -113,6 +113,8 @@ def test_iteration_history_tracks_oracle(N, k, q):
     assert np.all(rel <= 1e-4), rel
     tr = g[:early, 1] == 1
     np.testing.assert_allclose(g[:early][tr, 3], o[:early][tr, 3], rtol=1e-12)
+    # active columns per iteration: all k at first, never growing (locking only removes columns)
+    assert g[0, 4] == k and np.all(np.diff(g[:, 4]) <= 0) and np.all(g[:, 4] >= 1)
 
 
 LAM_TOL_MIXED = 1e-9
