@@ -133,7 +133,7 @@ def _host_cores():
     return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
 
 
-ORACLE_COMPONENTS = ("orth", "rr", "H", "precond", "project", "blocks", "resid")
+ORACLE_COMPONENTS = ("orth", "rr", "H", "precond", "project", "blocks", "resid", "copy")
 
 
 class OracleCost:
@@ -161,14 +161,16 @@ class OracleCost:
             rng = np.random.default_rng(w.seed + 17)
             self._X = oracle.orth(np.asfortranarray(self.X0))
             shape = self._X.shape
-            r = lambda: np.asfortranarray(rng.standard_normal(shape) + (1j * rng.standard_normal(shape)
-                                                                        if np.iscomplexobj(self._X) else 0.0))
-            self._W, self._P = r(), r()
+            cplx = np.iscomplexobj(self._X)
+            r = lambda: rng.standard_normal(shape) + (1j * rng.standard_normal(shape) if cplx else 0.0)
+            # W and P in the memory order they have inside the oracle's loop (W = A X - X M and P = the block
+            # update's output are row-major numpy results), so their column slices cost what they cost there
+            self._W, self._P = np.ascontiguousarray(r()), np.ascontiguousarray(r())
         return self._X, self._W, self._P
 
     def time_component(self, name):
-        """Seconds of one oracle component at full width on this workload (the sub-block loop over a slice of
-        the sub-blocks, scaled to all of them)."""
+        """Seconds of one oracle component at full width on this workload, with the data layouts and copies of
+        its loop (the sub-block loop over a slice of the sub-blocks, scaled to all of them)."""
         import oracle
         w = self.w
         theta = w.theta if w.dtype == "c128" else None
@@ -180,22 +182,31 @@ class OracleCost:
         if name == "orth":
             oracle.orth(np.asfortranarray(self.X0))
         elif name == "rr":
-            Xf, lam = oracle.rayleigh_ritz(X, Hop)
+            S = np.hstack([X, X[:, :0]])
+            Xf, lam = oracle.rayleigh_ritz(S, Hop)
             Wf = oracle.residual(Xf, Hop(Xf), lam)
             np.linalg.norm(Wf, axis=0)
+            Pfull = np.zeros(P.shape, dtype=P.dtype)
+            Pfull[:, list(range(kt))] = P
+            np.asfortranarray(Pfull[:, list(range(kt))])
         elif name == "H":
             Hop(X)
         elif name == "precond":
             oracle.precondition(W, self.V, N, h, 0.0, 0.1 / (h * h))
         elif name == "project":
-            oracle.project(W, X)
+            oracle.project(oracle.project(W, X), X[:, :0])
+        elif name == "copy":
+            X[:, list(range(kt))]
         elif name == "blocks":
             blocks = oracle.subblocks(kt, q)
             take = blocks[:max(1, len(blocks) // 8)]
+            Xn, Pn = np.empty_like(X), np.empty_like(W)
             for (a, b) in take:
                 Xj, Wj, Pj = X[:, a:b], W[:, a:b], P[:, a:b]
+                if np.any(np.linalg.norm(Pj, axis=0) == 0.0):
+                    Pj = None
                 CX, CW, CP = oracle.block_coefficients(Xj, Wj, Pj, Hop(Xj), Hop(Wj), Hop(Pj))
-                oracle.block_update(Xj, Wj, Pj, CX, CW, CP)
+                Xn[:, a:b], Pn[:, a:b] = oracle.block_update(Xj, Wj, Pj, CX, CW, CP)
             return (time.perf_counter() - t0) * len(blocks) / len(take)
         elif name == "resid":
             HX = Hop(X)
@@ -219,6 +230,7 @@ class OracleCost:
                 continue
             a = ka / kt
             total += (t["precond"] + t["blocks"]) * a + t["project"] * a * (1 if it == 1 else 2)
+            total += t["copy"] * (kt - ka) / kt                   # X_lock = X[:, J_lock] at every iteration
             if kind == 0:
                 total += (t["orth"] + t["resid"]) * a * a + t["H"] * a
             else:
@@ -354,6 +366,7 @@ FORMS = {
     "mixed_ozaki": ("mixed_tf32", "ozaki", "cholqr2"),
     "fp64_ozaki_polar": ("fp64", "ozaki", "polar"),
     "mixed_ozaki_polar": ("mixed_tf32", "ozaki", "polar"),
+    "mixed_bf16_ozaki": ("mixed_bf16", "ozaki", "cholqr2"),
 }
 FORM_TEXT = {
     "fp64": "FP64 throughout (FP64 FMA pipe GEMMs), CholeskyQR2",
@@ -363,6 +376,8 @@ FORM_TEXT = {
                    "on BF16 tcgen05 (Ozaki)",
     "fp64_ozaki_polar": "fp64_ozaki with the polar-series orthonormalisation of Section 5.5",
     "mixed_ozaki_polar": "mixed_ozaki with the polar-series orthonormalisation of Section 5.5",
+    "mixed_bf16_ozaki": "mixed with BF16 tcgen05 projections and first CholeskyQR Gram (FP32 accumulation), the "
+                        "other FP64 n x k GEMMs emulated on BF16 tcgen05 (Ozaki)",
 }
 # the FP64-accurate tensor-core form whose full solve stands in for each windowed form's iteration count
 WINDOW_PARTNER = {"fp64": "fp64_ozaki", "mixed": "mixed_ozaki"}
@@ -378,7 +393,7 @@ def main():
                     help="grid48_k1024 (default: the mixed-form workload), grid32_k256, grid16_k64, "
                          "grid32_k128_bloch (the complex Bloch recipe), batch64 (64 uneven problems)")
     ap.add_argument("--maxiter", type=int, default=6000)
-    ap.add_argument("--forms", default="mixed_ozaki,fp64_ozaki",
+    ap.add_argument("--forms", default="mixed_ozaki,fp64_ozaki,mixed_bf16_ozaki",
                     help="forms solved to tolerance; the first is the headline value (" + ", ".join(FORMS) + ")")
     ap.add_argument("--form-repeats", type=int, default=2, help="timed solves of each non-headline form")
     ap.add_argument("--window-forms", default="fp64,mixed",
@@ -817,7 +832,7 @@ def rooflines(pk, w, dev, stream, V_d, sk):
     ms_b = _time_ms(lambda: pk.ppcg_block_coefficients(hf.handle, X.data_ptr(), Wb.data_ptr(), Pb.data_ptr(),
                                                        HX.data_ptr(), HW.data_ptr(), HP.data_ptr(), n, k, 1,
                                                        coef.data_ptr(), flags.data_ptr()), stream, 5)
-    bflops = 2.0 * 21 * q * n * k          # both Gram triangles of the 3q x 3q pair: 2 x (3q)(3q+1)/2 dots per row
+    bflops = 18.0 * q * n * k              # per row and sub-block, both 3q x 3q Gram triangles: ~9 q^2 FMAs
     out["roofline_block_gram"] = {
         "kernel": f"block_gram_kernel + block_solve_kernel: 2 x (3q x 3q) Grams per sub-block, q={q}, {n} x {k}",
         "bound": "alu", "achieved": bflops / (ms_b / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -851,7 +866,7 @@ def run_e2e(pk, w, V, X0, steps, stream, form):
     opt = pk.ppcg_options()
     opt.maxiter = 6000
     prec, gm, orth = form
-    opt.precision = {"fp64": 0, "mixed_tf32": 1}[prec]
+    opt.precision = {"fp64": 0, "mixed_tf32": 1, "mixed_bf16": 2}[prec]
     opt.fp64_gemm = {"fma": 0, "ozaki": 1}[gm]
     opt.orth = {"cholqr2": 0, "polar": 1}[orth]
     h = pk.ppcg_create(op, n, k, w.sbsize, w.rr_period, opt, stream.cuda_stream)

@@ -46,6 +46,11 @@ typedef enum {
 
 typedef enum { PPCG_R64 = 0, PPCG_C128 = 1 } ppcg_dtype;
 
+/* Arithmetic of the GEMMs whose rounding only perturbs search directions: the projections of W and P (Alg. 3
+ * steps 9-10) and the Gram of the first CholeskyQR pass (step 18). PPCG_FP64: FP64. PPCG_MIXED_TF32 /
+ * PPCG_MIXED_BF16: tcgen05 tensor cores with TF32 / BF16 operands (converted from the FP64 blocks, round to nearest)
+ * and FP32 accumulation. Everything else (the sub-block Grams, step 20, the second CholeskyQR pass, the stencil, the
+ * small eigensolves and the Rayleigh-Ritz step) stays FP64 in every form. */
 typedef enum { PPCG_FP64 = 0, PPCG_MIXED_TF32 = 1, PPCG_MIXED_BF16 = 2 } ppcg_precision;
 
 /* The operator A = -Laplacian_h + diag(V). V may be a host or a device pointer; it is copied at create time

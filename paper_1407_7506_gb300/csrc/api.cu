@@ -42,6 +42,9 @@ struct ppcg_ctx {
   double *X = nullptr, *Xs = nullptr, *HX = nullptr, *W = nullptr, *HW = nullptr, *P = nullptr, *HP = nullptr;
   double *G = nullptr, *M = nullptr, *C = nullptr, *Rinv = nullptr, *lam = nullptr, *norms = nullptr;
   double* lamlk = nullptr;    // Ritz values of the locked columns (their Rayleigh-Ritz step), leading kl entries
+  double* tinv = nullptr;     // preconditioner diagonal 1 / max(dg - sigma, delta) for tinv_sigma
+  double tinv_sigma = 0.0;
+  bool tinv_valid = false;
   double *normpart = nullptr, *gpart = nullptr, *bpart = nullptr, *coef = nullptr, *cholws = nullptr,
          *jacws = nullptr;
   size_t gpart_cap = 0, bpart_cap = 0;
@@ -58,7 +61,8 @@ struct ppcg_ctx {
   int last_sweeps = 0;
   int eig_path = 0;           // route of the last dense_eigh: 0 Jacobi, 1 diagonal, 2 refined, 3 FP32 + refined
   int eig_count[4] = {0, 0, 0, 0};   // dense_eigh calls of the current solve per route
-  bool mixed = false;      // PPCG_MIXED_TF32: projections and the first CholQR Gram on tcgen05
+  bool mixed = false;      // PPCG_MIXED_TF32 / _BF16: projections and the first CholQR Gram on tcgen05
+  bool bf16 = false;       // PPCG_MIXED_BF16: those GEMMs take BF16 operands (else TF32)
   bool ozaki = false;      // FP64 n x k GEMMs emulated on the BF16 tensor cores (error-free splitting)
   int* ozexps = nullptr;   // exponent workspace of the emulated GEMMs
   uint8_t* ozimg = nullptr;   // digit images of the emulated Grams' operands
@@ -109,7 +113,7 @@ Sizes make_sizes(int64_t n, int kt, int q, bool ozaki) {
 
 // Offsets of every region; returns the total byte count.
 struct Offsets {
-  size_t V, dg, blk[7], G, M, C, Rinv, lam, lamlk, norms, normpart, gpart, bpart, coef, cholws, jacws;
+  size_t V, dg, tinv, blk[7], G, M, C, Rinv, lam, lamlk, norms, normpart, gpart, bpart, coef, cholws, jacws;
   size_t iflag, icnt, jinfo, idx, bflags, bar, ozexps, ozimg;
   size_t total;
 };
@@ -120,6 +124,7 @@ Offsets layout(const Sizes& s) {
   const size_t blk = (size_t)s.ld * s.kt;
   o.V = L.off(s.ld, 8);
   o.dg = L.off(s.ld, 8);
+  o.tinv = L.off(s.ld, 8);
   for (int i = 0; i < 7; ++i) o.blk[i] = L.off(blk, 8);
   const size_t kk = (size_t)s.kt * s.kt;
   o.G = L.off(kk, 8);
@@ -165,7 +170,8 @@ ppcg_status check_args(const ppcg_operator* op, int64_t n, int32_t k, int32_t sb
   if (2 * kt > n || f * kt > 65535) return PPCG_ERR_ARG;
   if (sbsize < 1 || f * sbsize > kMaxSbsize || sbsize > kt) return PPCG_ERR_ARG;
   if (opt && (opt->maxiter < 0 || opt->sigma_floor < 0.0)) return PPCG_ERR_ARG;
-  if (opt && opt->precision != PPCG_FP64 && opt->precision != PPCG_MIXED_TF32) return PPCG_ERR_UNSUPPORTED;
+  if (opt && opt->precision != PPCG_FP64 && opt->precision != PPCG_MIXED_TF32 && opt->precision != PPCG_MIXED_BF16)
+    return PPCG_ERR_UNSUPPORTED;
   if (opt && (opt->fp64_gemm < 0 || opt->fp64_gemm > 1)) return PPCG_ERR_ARG;
   if (opt && (opt->orth < 0 || opt->orth > 1)) return PPCG_ERR_ARG;
   if (opt && !(opt->orth_skip_tol >= 0.0 && std::isfinite(opt->orth_skip_tol))) return PPCG_ERR_ARG;
@@ -224,6 +230,9 @@ ppcg_status apply_H(ppcg_ctx* c, const double* X, int64_t ldx, double* Y, int64_
   return PPCG_OK;
 }
 
+constexpr int kProjectFuse = 128;   // W and P are projected as one block while together they have at most this many
+                                    // columns (there the projections are bound by reading X, not by arithmetic)
+
 // FP64 Gram over the n grid rows: FP64 pipe, or the FP64-accurate tensor-core emulation when selected
 ppcg_status gram(ppcg_ctx* c, const double* A, int64_t lda, const double* B, int64_t ldb, int ma, int mb,
                  double* Cm, int ldc) {
@@ -265,7 +274,8 @@ ppcg_status residual_m(ppcg_ctx* c, const double* X, const double* HX, int64_t l
 ppcg_status gram_tc(ppcg_ctx* c, const double* A, int64_t lda, const double* B, int64_t ldb, int ma, int mb,
                     double* Cm, int ldc) {
   const bool sym = (A == B && lda == ldb && ma == mb);
-  CK(ppcg::tc_gram(A, lda, B, ldb, c->n, ma, mb, Cm, ldc, sym, c->gpart, c->gpart_cap, c->tcflag, c->stream));
+  CK(ppcg::tc_gram(A, lda, B, ldb, c->n, ma, mb, Cm, ldc, sym, c->gpart, c->gpart_cap, c->tcflag, c->stream,
+                   c->bf16));
   return PPCG_OK;
 }
 
@@ -275,7 +285,7 @@ ppcg_status project(ppcg_ctx* c, const double* X, int64_t ldx, int mx, double* Y
   if (mx <= 0 || my <= 0) return PPCG_OK;
   if (c->mixed) {
     PS(gram_tc(c, X, ldx, Y, ldy, mx, my, c->G, mx));
-    CK(tc_update(X, ldx, c->G, mx, c->n, mx, my, Y, ldy, true, c->tcflag, c->stream));
+    CK(tc_update(X, ldx, c->G, mx, c->n, mx, my, Y, ldy, true, c->tcflag, c->stream, c->bf16));
     return PPCG_OK;
   }
   PS(gram(c, X, ldx, Y, ldy, mx, my, c->G, mx));
@@ -422,6 +432,13 @@ ResidualArgs resid_args(ppcg_ctx* c, double sigma) {
   ra.sigma = sigma;
   ra.delta = c->delta;
   ra.norm_part = c->normpart;
+  // the preconditioner diagonal changes only with sigma (once per Rayleigh-Ritz step): form it once
+  if (!(c->tinv_valid && c->tinv_sigma == sigma) &&
+      precond_diag(c->dg, sigma, c->delta, c->n, c->tinv, c->stream) == cudaSuccess) {
+    c->tinv_valid = true;
+    c->tinv_sigma = sigma;
+  }
+  ra.tinv = (c->tinv_valid && c->tinv_sigma == sigma) ? c->tinv : nullptr;
   return ra;
 }
 
@@ -469,7 +486,21 @@ ppcg_status rr_step(ppcg_ctx* c, SolveState& st, bool allow_compact, ppcg_stats*
     PS(gram(c, c->X, c->ld, c->HX, c->ld, kt, kt, c->M, kt));           // S^T A S
   }
   CK(cudaMemsetAsync(rrflag, 0, sizeof(int), s));
-  CK(chol_inv(c->G, kt, 0.0, c->Rinv, c->cholws, rrflag, c->bar, s));  // R^{-1}
+  if (kl > 0) {
+    // S^T S = [[I, G_la], [G_la^T, G_aa]] = R^T R with R = [[I, G_la], [0, Ra]], Ra^T Ra = G_aa - G_la^T G_la:
+    // only the k_act x k_act Schur complement is factorised
+    const int ka = kt - kl;
+    const double* Gla = c->G + (int64_t)kl * kt;
+    double* Gs = c->jacws;                                   // scratch until the eigensolve
+    double* Rainv = c->jacws + (int64_t)ka * ka;
+    CK(kxk_gemm(kxk(c), true, Gla, kt, Gla, kt, ka, ka, kl, c->C, ka, s));          // G_la^T G_la
+    CK(locked_schur(c->G, kt, kl, c->C, kCholPivotTol, Gs, rrflag, s));
+    CK(chol_inv(Gs, ka, 0.0, Rainv, c->cholws, rrflag, c->bar, s));
+    CK(kxk_gemm(kxk(c), false, Gla, kt, Rainv, ka, kl, ka, ka, c->C, kl, s));       // U = G_la Ra^{-1}
+    CK(locked_rinv_fill(c->Rinv, kt, kl, c->C, Rainv, s));
+  } else {
+    CK(chol_inv(c->G, kt, 0.0, c->Rinv, c->cholws, rrflag, c->bar, s));  // R^{-1}
+  }
   // K = R^{-T} (S^T A S) R^{-1}: T = (S^T A S) R^{-1} (R^{-1} upper: trimmed K loop), K = (R^{-1})^T T
   CK(kxk_gemm(kxk(c), false, c->M, kt, c->Rinv, kt, kt, kt, kt, c->G, kt, s));
   CK(kxk_gemm(kxk(c), true, c->Rinv, kt, c->G, kt, kt, kt, kt, c->M, kt, s));
@@ -681,6 +712,7 @@ ppcg_status ppcg_create(const ppcg_operator* op, int64_t n, int32_t k, int32_t s
   auto I = [&](size_t off) { return reinterpret_cast<int*>(b + off); };
   c->V = D(o.V);
   c->dg = D(o.dg);
+  c->tinv = D(o.tinv);
   for (int i = 0; i < 7; ++i) c->blk[i] = D(o.blk[i]);
   c->X = c->blk[0]; c->Xs = c->blk[1]; c->HX = c->blk[2]; c->W = c->blk[3];
   c->HW = c->blk[4]; c->P = c->blk[5]; c->HP = c->blk[6];
@@ -691,7 +723,8 @@ ppcg_status ppcg_create(const ppcg_operator* op, int64_t n, int32_t k, int32_t s
   c->iflag = I(o.iflag); c->icnt = I(o.icnt); c->jinfo = I(o.jinfo); c->idx = I(o.idx); c->bflags = I(o.bflags);
   c->bar = reinterpret_cast<unsigned*>(b + o.bar);
   c->tcflag = c->icnt + 2;
-  c->mixed = (c->opt.precision == PPCG_MIXED_TF32);
+  c->mixed = (c->opt.precision == PPCG_MIXED_TF32 || c->opt.precision == PPCG_MIXED_BF16);
+  c->bf16 = (c->opt.precision == PPCG_MIXED_BF16);
   c->ozaki = (c->opt.fp64_gemm == 1);
   c->ozexps = reinterpret_cast<int*>(b + o.ozexps);
   c->ozimg = sz.ozimg_bytes ? reinterpret_cast<uint8_t*>(b + o.ozimg) : nullptr;
@@ -711,6 +744,7 @@ ppcg_status ppcg_set_potential(ppcg_handle c, const double* V) {
   if (!c || !V) return PPCG_ERR_ARG;
   CK(cudaMemcpyAsync(c->V, V, sizeof(double) * c->ng, cudaMemcpyDefault, c->stream));
   CK(make_diag(c->V, c->grid.inv_h2, c->ng, c->dg, c->stream));
+  c->tinv_valid = false;
   if (c->cplx)   // the real form's diagonal is diag(A) twice
     CK(cudaMemcpyAsync(c->dg + c->ng, c->dg, sizeof(double) * c->ng, cudaMemcpyDeviceToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -775,8 +809,19 @@ ppcg_status ppcg_solve(ppcg_handle c, const double* X0, double tol, double* lamb
     // step 8 is fused into the residual of the previous step (W already holds T R)
     // steps 9-10: project W and P against [X_lock, X]
     phase_mark(c, PPCG_T_GEMM);
-    PS(project(c, c->X, ld, kt, c->W, ld, ka));
-    if (st.has_p) PS(project(c, c->X, ld, kt, c->P, ld, ka));
+    if (st.has_p && 2 * ka <= kProjectFuse && 2 * ka <= kt) {
+      // few active columns: the projections read all k_t columns of X for only 2 k_act columns of work, so W and P
+      // are projected as one block [W, P] (staged in Xs, free until step 18): X is read twice instead of four times
+      const size_t pitch = ld * sizeof(double), rows = n * sizeof(double);
+      CK(cudaMemcpy2DAsync(c->Xs, pitch, c->W, pitch, rows, ka, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpy2DAsync(c->Xs + (int64_t)ka * ld, pitch, c->P, pitch, rows, ka, cudaMemcpyDeviceToDevice, s));
+      PS(project(c, c->X, ld, kt, c->Xs, ld, 2 * ka));
+      CK(cudaMemcpy2DAsync(c->W, pitch, c->Xs, pitch, rows, ka, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpy2DAsync(c->P, pitch, c->Xs + (int64_t)ka * ld, pitch, rows, ka, cudaMemcpyDeviceToDevice, s));
+    } else {
+      PS(project(c, c->X, ld, kt, c->W, ld, ka));
+      if (st.has_p) PS(project(c, c->X, ld, kt, c->P, ld, ka));
+    }
     phase_mark(c, PPCG_T_AX);
     PS(apply_H(c, c->W, ld, c->HW, ld, ka));
     if (st.has_p) PS(apply_H(c, c->P, ld, c->HP, ld, ka));

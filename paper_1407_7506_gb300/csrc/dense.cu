@@ -507,16 +507,21 @@ __global__ void symmetrize_kernel(const double* __restrict__ M, int m, double* _
   }
 }
 
-// ||M||_F and max_{i != j} |M_ij| (one CTA: a fixed summation order, so repeated calls agree bit for bit)
-__global__ void eig_stats_kernel(const double* __restrict__ M, int m, double* out) {
-  double s = 0.0, mx = 0.0;
+// ||M||_F and max_{i != j} |M_ij| in two passes with a fixed summation order (repeated calls agree bit for bit):
+// each CTA reduces a contiguous range into part[2 b], part[2 b + 1]; one CTA then combines the nb partials in order.
+constexpr int kStatBlocks = 256;
+
+__global__ void __launch_bounds__(256) eig_stats_part_kernel(const double* __restrict__ M, int m, double* part) {
   const int64_t cnt = (int64_t)m * m;
-  for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+  const int64_t per = ceil_div(cnt, (int64_t)gridDim.x);
+  const int64_t e0 = (int64_t)blockIdx.x * per, e1 = min(cnt, e0 + per);
+  double s = 0.0, mx = 0.0;
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const double v = M[e];
     s += v * v;
     if (e % m != e / m) mx = fmax(mx, fabs(v));
   }
-  __shared__ double rs[1024], rm[1024];
+  __shared__ double rs[256], rm[256];
   rs[threadIdx.x] = s;
   rm[threadIdx.x] = mx;
   __syncthreads();
@@ -528,9 +533,20 @@ __global__ void eig_stats_kernel(const double* __restrict__ M, int m, double* ou
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    out[0] = sqrt(rs[0]);
-    out[1] = rm[0];
+    part[2 * blockIdx.x] = rs[0];
+    part[2 * blockIdx.x + 1] = rm[0];
   }
+}
+
+__global__ void eig_stats_kernel(const double* __restrict__ part, int nb, double* out) {
+  if (threadIdx.x != 0) return;
+  double s = 0.0, mx = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    s += part[2 * b];
+    mx = fmax(mx, part[2 * b + 1]);
+  }
+  out[0] = sqrt(s);
+  out[1] = mx;
 }
 
 // ---------------------------------------------------------------------------------- eigenvector refinement
@@ -589,34 +605,24 @@ __global__ void refine_coupling_kernel(const double* __restrict__ S, const doubl
   if ((threadIdx.x & 31) == 0) atomic_max_nonneg(stat + 4, mx);
 }
 
-// Clusters: sort lam (strict order (value, index), NaN as +inf), cut the sorted sequence where consecutive values
-// differ by more than gap = max(kClusterGap x coupling, kClusterFloor ||M||_F), and number the runs of two or more.
-// order[r] = index of the r-th smallest; cid[i] = cluster of i or -1; cluster c = order[cls[c] .. cls[c] + cln[c]).
-// One CTA of 1024 threads; the cut positions are a bitmask in shared memory (kt <= 65535 columns).
+// Clusters: with order[r] the index of the r-th smallest lam and ls[r] its value (rank_sort_kernel: strict order
+// (value, index), NaN as +inf), cut the sorted sequence where consecutive values differ by more than
+// gap = max(kClusterGap x coupling, kClusterFloor ||M||_F), and number the runs of two or more.
+// cid[i] = cluster of i or -1; cluster c = order[cls[c] .. cls[c] + cln[c]). One CTA of 1024 threads; the cut
+// positions are a bitmask in shared memory (kt <= 65535 columns).
 __global__ void __launch_bounds__(1024)
-refine_cluster_kernel(const double* __restrict__ lam, int m, double* stat, int* order, int* cid, int* cls,
-                      int* cln) {
+refine_cluster_kernel(const double* __restrict__ ls, const int* __restrict__ order, int m, double* stat, int* cid,
+                      int* cls, int* cln) {
   __shared__ unsigned cut[2048];
   const double coupling = stat[4];
   const double gap = fmax(kClusterGap * coupling, kClusterFloor * stat[0]);
   for (int w = threadIdx.x; w < 2048; w += blockDim.x) cut[w] = 0u;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    const double li = lam[i];
-    const double ki = isnan(li) ? CUDART_INF : li;
-    int rank = 0;
-    for (int l = 0; l < m; ++l) {
-      const double ll = lam[l];
-      const double kl = isnan(ll) ? CUDART_INF : ll;
-      rank += (kl < ki || (kl == ki && l < i)) ? 1 : 0;
-    }
-    order[rank] = i;
-    cid[i] = -1;
-  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) cid[i] = -1;
   __syncthreads();
   for (int r = threadIdx.x; r < m; r += blockDim.x) {
     bool c = true;
     if (r > 0) {
-      const double d = lam[order[r]] - lam[order[r - 1]];
+      const double d = ls[r] - ls[r - 1];
       c = !(d <= gap);                               // NaN or inf: a cut
     }
     if (c) atomicOr(&cut[r >> 5], 1u << (r & 31));
@@ -1063,8 +1069,9 @@ cudaError_t dense_eigh_auto(const double* Min, int m, double* lambda, double* C,
   symmetrize_kernel<<<grid_for((int64_t)m * m), 256, 0, s>>>(Min, m, msym);
   count_launch();
   cudaError_t e;
-  eig_stats_kernel<<<1, 1024, 0, s>>>(M, m, w.stat);
-  count_launch();
+  eig_stats_part_kernel<<<kStatBlocks, 256, 0, s>>>(M, m, w.E);
+  eig_stats_kernel<<<1, 32, 0, s>>>(w.E, kStatBlocks, w.stat);
+  count_launch(2);
   double h[8] = {};
   if ((e = cudaMemcpyAsync(h, w.stat, 2 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
@@ -1102,10 +1109,11 @@ cudaError_t dense_eigh_auto(const double* Min, int m, double* lambda, double* C,
     }
     refine_diag_kernel<<<1, 1024, 0, s>>>(St, Gt, m, w.lam, w.stat);
     refine_coupling_kernel<<<grid_for(cnt), 256, 0, s>>>(St, Gt, m, w.lam, w.stat);
-    refine_cluster_kernel<<<1, 1024, 0, s>>>(w.lam, m, w.stat, w.order, w.cid, w.cls, w.cln);
+    rank_sort_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(w.lam, 1, m, w.lam + w.mp, w.order);
+    refine_cluster_kernel<<<1, 1024, 0, s>>>(w.lam + w.mp, w.order, m, w.stat, w.cid, w.cls, w.cln);
     refine_coef_kernel<<<grid_for(cnt), 256, 0, s>>>(St, Gt, m, w.lam, w.cid, thr, w.stat, w.E);
     refine_cluster_eig_kernel<<<gcl, 256, 0, s>>>(St, Gt, m, w.lam, w.order, w.cls, w.cln, w.stat, w.E);
-    count_launch(5);
+    count_launch(6);
     if (t == 0 && from_identity) {
       identity_plus_kernel<<<grid_for(cnt), 256, 0, s>>>(w.E, m, w.Z);
       count_launch();

@@ -143,7 +143,7 @@ gemm_nn_kernel(const double* __restrict__ A, int64_t lda, const double* __restri
     const int64_t r = r0 + tr * 4 + i;
     if (r >= n) continue;
     double tinv = 0.0;
-    if (epi == (int)Epi::Residual) tinv = 1.0 / fmax(ra.dg[r] - ra.sigma, ra.delta);
+    if (epi == (int)Epi::Residual) tinv = ra.tinv ? ra.tinv[r] : 1.0 / fmax(ra.dg[r] - ra.sigma, ra.delta);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int c = c0 + tc * 4 + j;

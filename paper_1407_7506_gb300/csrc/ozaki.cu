@@ -6,8 +6,9 @@
 // integer T = round(x 2^(54 - E)) and written as 8 balanced base-128 digits d_j in [-63, 64]:
 //   x = sum_{j<8} d_j 2^(E - 5 - 7 j)  (to 2^-55 relative to the column maximum).
 // A digit is exact in BF16 and a digit product is at most 2^12, so the 36 digit-pair products with
-// j + l = g (g = 0..7) can share one FP32 TMEM accumulator: over a chunk of 256 summed terms each group stays an
-// integer below 2^23 and the tensor-core accumulation is exact. After every chunk the 8 group accumulators are
+// j + l = g (g = 0..7) can share one FP32 TMEM accumulator: over a chunk of 512 summed terms each group stays an
+// integer of magnitude at most 8 * 512 * 2^12 = 2^24, every partial sum is an integer that FP32 represents exactly,
+// and the tensor-core accumulation is exact. After every chunk the 8 group accumulators are
 // folded, with weights 2^(-7 g), into a double-float (FP32 pair) register accumulator; one FP64 scale by
 // 2^(E_a + E_b - 10) per element produces the result. The error is that of the 55-bit digits plus the ~2^-48
 // relative rounding of the double-float sum, below the rounding of an FP64 GEMM of these lengths.
@@ -36,7 +37,7 @@ constexpr int kN = 64;
 constexpr int kDig = 8;                   // digits per element
 constexpr int kGroups = 8;                // g = j + l <= 7
 constexpr int kBK = 32;                   // K per stage (2 MMAs of K = 16)
-constexpr int kChunk = 256;               // exact-accumulation chunk (8 * 256 * 2^12 = 2^23)
+constexpr int kChunk = 512;               // exact-accumulation chunk (8 * 512 * 2^12 = 2^24: FP32-exact integers)
 constexpr int kThreads = 256;
 constexpr uint32_t kLBO = 128;            // bytes between core matrices along K (8 bf16)
 constexpr uint32_t kSBO = (kBK / 8) * 128;  // bytes between 8-row groups
@@ -500,7 +501,7 @@ constexpr uint32_t kSAPlane = 2 * kSImg;                 // 128 rows
 constexpr uint32_t kSBPlane = kSImg;                     // 64 rows
 constexpr uint32_t kSStage = kDig * (kSAPlane + kSBPlane);   // 48 KB
 constexpr int kSBuf = 4;
-constexpr int kSChunkBlocks = kChunk / kSK;             // 16 stages per exact-accumulation chunk
+constexpr int kSChunkBlocks = kChunk / kSK;             // 32 stages per exact-accumulation chunk
 
 __device__ __forceinline__ uint32_t tile_off16(int row, int k) {
   return (uint32_t)(row >> 3) * kSSBO + (uint32_t)(row & 7) * 16u + (uint32_t)(k >> 3) * 128u + (uint32_t)(k & 7) * 2u;

@@ -21,7 +21,7 @@ constexpr int kRefineSteps = 4;          // refinement steps before falling back
 constexpr double kRefineAccept = 1e-8;   // accept a refinement step whose largest |E_ij| (i != j) is at most this
 constexpr double kJacobiTol32 = 3e-7;    // single-precision Jacobi (start of the refinement): rotate while
                                          // |a_pq| > kJacobiTol32 ||A||_F
-constexpr int kJacobiMaxSweeps32 = 16;
+constexpr int kJacobiMaxSweeps32 = 10;    // its rounding floor is reached by then
 constexpr double kClusterGap = 4.0;      // refinement: eigenvalues closer than kClusterGap x the largest coupling
                                          // |S_ij + lam_j R_ij| form a cluster, solved as one small eigenproblem
 constexpr double kClusterFloor = 1e-7;   // ... and always those closer than kClusterFloor ||M||_F: there rounding in
@@ -71,7 +71,10 @@ struct ResidualArgs {
   double sigma;         // preconditioner shift
   double delta;         // preconditioner floor
   double* norm_part;    // [row tiles][p] partial column norms^2
+  const double* tinv;   // 1 / max(dg - sigma, delta) per row, precomputed (may be NULL: formed in the kernel)
 };
+// tinv[r] = 1 / max(dg[r] - sigma, delta): the preconditioner diagonal, formed once per shift
+cudaError_t precond_diag(const double* dg, double sigma, double delta, int64_t n, double* tinv, cudaStream_t s);
 // Store:    Y = A G
 // Sub:      Y = Y - A G                       (in place)
 // Residual: R = Yin - A G; Y = T R; norm_part = per-tile column sums of R^2
@@ -84,13 +87,14 @@ int64_t norm_row_tiles(int64_t n);   // row tiles of gemm_nn / residual_diag (no
 cudaError_t gram_reduce_partials(const double* part, int nsplit, int ma, int mb, double* C, int ldc, bool symmetric,
                                  cudaStream_t s);
 
-// ---------------------------------------------------------------------------------------------- tcgen05 (TF32)
-// Same contracts as gram / gemm_nn (Sub or Store), with TF32 inputs and FP32 accumulation on the tensor cores.
-// *flag receives kFlagTimeout if a bounded mbarrier wait gave up.
+// ---------------------------------------------------------------------------------------------- tcgen05 (TF32/BF16)
+// Same contracts as gram / gemm_nn (Sub or Store), with TF32 (bf16 = false) or BF16 (bf16 = true) inputs and FP32
+// accumulation on the tensor cores. *flag receives kFlagTimeout if a bounded mbarrier wait gave up.
 cudaError_t tc_gram(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n, int ma, int mb, double* C,
-                    int ldc, bool symmetric, double* part, size_t part_capacity, int* flag, cudaStream_t s);
+                    int ldc, bool symmetric, double* part, size_t part_capacity, int* flag, cudaStream_t s,
+                    bool bf16 = false);
 cudaError_t tc_update(const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p, double* Y,
-                      int64_t ldy, bool subtract, int* flag, cudaStream_t s);
+                      int64_t ldy, bool subtract, int* flag, cudaStream_t s, bool bf16 = false);
 
 // ---------------------------------------------------------------------------------------------- Ozaki (FP64)
 // FP64-accurate versions of gram / gemm_nn (Store or Sub) on the BF16 tensor cores by error-free splitting.
@@ -134,6 +138,12 @@ cudaError_t density_c(const double* Z, int64_t ldz, int64_t n, int k, double sca
 // Rayleigh-Ritz Grams with kl locked leading columns: G[0:kl, 0:kl] = I, M[0:kl, 0:kl] = diag(lam_lock), and the
 // lower-left blocks G[kl:, 0:kl], M[kl:, 0:kl] mirrored from the computed upper-right ones (m x m, ld m).
 cudaError_t locked_gram_fill(double* G, double* M, int m, int kl, const double* lam_lock, cudaStream_t s);
+// Cholesky of a Gram with kl locked leading columns, G = [[I, G_la], [G_la^T, G_aa]]: the Schur complement
+// Gs = G_aa - T (T = G_la^T G_la, ka x ka) with a breakdown flag for a pivot below pivot_tol^2 G_aa,ii, and
+// R^{-1} = [[I, -U], [0, Ra^{-1}]] assembled from U = G_la Ra^{-1} (kl x ka) and Ra^{-1} (ka x ka, upper).
+cudaError_t locked_schur(const double* G, int kt, int kl, const double* T, double pivot_tol, double* Gs, int* flag,
+                         cudaStream_t s);
+cudaError_t locked_rinv_fill(double* Rinv, int kt, int kl, const double* U, const double* Rainv, cudaStream_t s);
 cudaError_t eye_residual(double* G, int m, double* fro2, cudaStream_t s);
 cudaError_t scaled_plus_identity(const double* Y, int m, double a, double b, double* Z, cudaStream_t s);
 cudaError_t add_diag(double* Z, int m, double b, cudaStream_t s);

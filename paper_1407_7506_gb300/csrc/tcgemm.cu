@@ -1,7 +1,10 @@
-// Tensor-core (tcgen05, TF32 inputs, FP32 accumulation in TMEM) versions of the tall-skinny GEMMs whose
+// Tensor-core (tcgen05, TF32 or BF16 inputs, FP32 accumulation in TMEM) versions of the tall-skinny GEMMs whose
 // rounding only perturbs search directions: the projections of steps 9-10 (G = X^T W, W <- W - X G) and the
 // Gram of the first CholeskyQR pass (its error changes only the conditioning of R, not span(X), because
-// X R^{-1} is applied in FP64). This is the mixed-precision form of the method's workload.
+// X R^{-1} is applied in FP64). These are the mixed-precision forms of the method's workload: kind::tf32 with
+// K = 8 per instruction, or kind::f16 with BF16 operands and K = 16 per instruction. Both stage 128 bytes of K per
+// tile row (32 TF32 or 64 BF16 values), so the shared-memory layout, the descriptors and the four instructions per
+// stage are the same; only the conversion and the element packing differ.
 //
 // The blocks are FP64 in HBM, which TMA cannot convert, so the operand tiles are staged by the threads: FP64
 // loads, conversion to TF32 (round to nearest, by integer operations on the upper word), and stores into shared memory in the K-major layout with the
@@ -30,7 +33,9 @@ namespace {
 using namespace tc;
 
 constexpr int kM = 128;           // MMA M: rows of the accumulator = TMEM lanes
-constexpr int kBK = 32;           // K elements staged per stage (4 MMAs of K = 8): one 128-byte swizzle atom
+constexpr int kBK = 32;           // TF32 K elements staged per stage (4 MMAs of K = 8): one 128-byte swizzle atom
+template <bool BF>
+constexpr int kbk() { return BF ? 64 : 32; }   // K elements per stage: 128 bytes of TF32 or BF16
 constexpr int kThreads = 512;     // 16 warps: 4 per scheduler, to hide the latency of the integer conversions
 constexpr int kWarps = kThreads / 32;
 constexpr uint32_t kRowB = 128;   // bytes per tile row (kBK TF32 values)
@@ -39,6 +44,10 @@ constexpr uint32_t kSBO = 1024;   // bytes between 8-row groups
 // byte offset of element (row, k) of a stage tile: row-major 128-byte rows, 16-byte chunks XOR-swizzled by row mod 8
 __device__ __forceinline__ uint32_t tile_off(int row, int k) {
   return (uint32_t)row * kRowB + ((uint32_t)((k >> 2) ^ (row & 7)) << 4) + (uint32_t)(k & 3) * 4u;
+}
+// the same for 2-byte (BF16) elements: 8 per 16-byte chunk
+__device__ __forceinline__ uint32_t tile_off_bf(int row, int k) {
+  return (uint32_t)row * kRowB + ((uint32_t)((k >> 3) ^ (row & 7)) << 4) + (uint32_t)(k & 7) * 2u;
 }
 
 // shared-memory descriptor of a K-major tile with the 128-byte swizzle (layout code 2 in bits 61-63); the tile is
@@ -71,6 +80,22 @@ __device__ __forceinline__ uint32_t tf32_from_hi(uint32_t hi) {
   return f | (hi & 0x80000000u);
 }
 
+// BF16 bit pattern of the value nearest to the double whose upper word is hi, ties away from zero: the same
+// integer rebias to the FP32 layout, then the FP32 pattern rounded to its upper 16 bits (8 significant bits; the
+// upper word keeps 20 mantissa bits, enough to decide this rounding). Below the FP32 normal range: zero; above it:
+// infinity (NaN stays non-finite).
+__device__ __forceinline__ uint32_t bf16_from_hi(uint32_t hi) {
+  const uint32_t mag = hi & 0x7FFFFFFFu;
+  uint32_t b = ((((mag - 0x38000000u) << 3) + 0x8000u) >> 16) & 0x7FFFu;
+  if (mag < 0x38100000u) b = 0u;
+  if (mag >= 0x47F00000u) b = mag > 0x7FF00000u ? 0x7FC0u : 0x7F80u;
+  return b | ((hi >> 16) & 0x8000u);
+}
+
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 // upper 32-bit word of a double in global memory (little-endian: at byte offset 4)
 __device__ __forceinline__ uint32_t ld_hi(const double* p) {
   return __ldg(reinterpret_cast<const uint32_t*>(p) + 1);
@@ -89,7 +114,7 @@ struct TcSmem {
 // Returns false (uniformly) if a bounded wait gave up; TMEM is still allocated on return (caller frees it).
 // The A tile has MT halves of 128 rows, each with its own accumulator of NT TMEM columns (at column h NT), and
 // every staged B tile feeds all of them.
-template <class Regs, int MT, int NT, class LoadFn, class StoreFn>
+template <class Regs, int MT, int NT, bool BF, class LoadFn, class StoreFn>
 __device__ bool tc_mainloop(int nk, uint8_t* tiles, uint32_t a_bytes, uint32_t b_bytes, TcSmem& sm, uint32_t tmem,
                             uint32_t idesc, LoadFn load, StoreFn store) {
   const int tid = threadIdx.x;
@@ -113,11 +138,14 @@ __device__ bool tc_mainloop(int nk, uint8_t* tiles, uint32_t a_bytes, uint32_t b
       tc_fence_after();
       const uint32_t a0 = smem_u32(a_tile), b0 = smem_u32(b_tile);
 #pragma unroll
-      for (int j = 0; j < kBK / 8; ++j)
+      for (int j = 0; j < 4; ++j)                    // 32 bytes of K per instruction (8 TF32 or 16 BF16)
 #pragma unroll
-        for (int h = 0; h < MT; ++h)
-          mma_tf32(tmem + (uint32_t)(h * NT), smem_desc(a0 + h * kM * kRowB + j * 32), smem_desc(b0 + j * 32), idesc,
-                   (kb > 0 || j > 0) ? 1u : 0u);
+        for (int h = 0; h < MT; ++h) {
+          const uint64_t ad = smem_desc(a0 + h * kM * kRowB + j * 32), bd = smem_desc(b0 + j * 32);
+          const uint32_t acc = (kb > 0 || j > 0) ? 1u : 0u;
+          if (BF) mma_bf16(tmem + (uint32_t)(h * NT), ad, bd, idesc, acc);
+          else mma_tf32(tmem + (uint32_t)(h * NT), ad, bd, idesc, acc);
+        }
       mma_commit(smem_u32(&sm.mbar[s]));
     }
     return true;
@@ -169,10 +197,10 @@ __device__ void tc_teardown(TcSmem& sm, uint32_t tmem, uint32_t ncols, bool ok, 
 
 // Per-thread register staging: all global loads of a stage are issued before any is converted and stored, and the
 // next stage's loads are issued while the MMAs run.
-template <int NT, int MT>
+template <int NT, int MT, bool BF>
 struct Stage {
-  static constexpr int kA = MT * kM * kBK / kThreads;    // elements of A per thread
-  static constexpr int kB = NT * kBK / kThreads;    // elements of B per thread
+  static constexpr int kA = MT * kM * kbk<BF>() / kThreads;    // elements of A per thread
+  static constexpr int kB = NT * kbk<BF>() / kThreads;         // elements of B per thread
   uint32_t a[kA];   // upper words of the FP64 elements
   uint32_t b[kB];
 };
@@ -184,48 +212,65 @@ __device__ __forceinline__ uint8_t* align_tiles(uint8_t* dyn) {
 
 // ------------------------------------------------------------------------------------------ C = A^T B partials
 // grid (tiles_m * tiles_n, nsplit); tile rows m0 = tm * 128 MT (columns of A), cols n0 = tn * NT (columns of B)
-template <int NT, int MT>
+template <int NT, int MT, bool BF>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_gram_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ B, int64_t ldb, int64_t n,
                int ma, int mb, int tiles_n, int64_t rows_per_split, float* __restrict__ part, int* flag) {
-  using Regs = Stage<NT, MT>;
+  using Regs = Stage<NT, MT, BF>;
+  constexpr int BK = kbk<BF>();
   extern __shared__ __align__(1024) uint8_t dyn[];
   __shared__ TcSmem sm;
   const int tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
   const int m0 = tm * kM * MT, n0 = tn * NT;
   const int64_t r_begin = (int64_t)blockIdx.y * rows_per_split;
   const int64_t r_end = min(n, r_begin + rows_per_split);
-  const int nk = r_end > r_begin ? (int)ceil_div(r_end - r_begin, kBK) : 0;
+  const int nk = r_end > r_begin ? (int)ceil_div(r_end - r_begin, BK) : 0;
   constexpr uint32_t a_bytes = MT * kM * kRowB, b_bytes = (uint32_t)NT * kRowB;
   constexpr uint32_t ncols = (uint32_t)(MT * NT);
   tc_setup(sm, ncols);
   const uint32_t tmem = sm.tmem_slot;
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
-  // lane = k (a row of A and B), warp w takes tile rows w, w + 16, ...: 256 contiguous bytes per warp load
+  // TF32: lane = k (a row of A and B), warp w takes tile rows w, w + 16, ...: 256 contiguous bytes per warp load.
+  // BF16: lane = the pair of rows k = 2 lane, 2 lane + 1 (512 contiguous bytes per warp), packed into one word.
+  constexpr int P = BF ? 2 : 1;
   auto load = [&](int kb, Regs& reg) {
-    const int64_t r = r_begin + (int64_t)kb * kBK + lane;
-    const bool rin = r < r_end;
+    const int64_t r = r_begin + (int64_t)kb * BK + P * lane;
 #pragma unroll
-    for (int i = 0; i < Regs::kA; ++i) {
+    for (int i = 0; i < Regs::kA / P; ++i) {
       const int col = m0 + warp + kWarps * i;
-      reg.a[i] = (rin && col < ma) ? ld_hi(A + r + (int64_t)col * lda) : 0u;
+#pragma unroll
+      for (int e = 0; e < P; ++e)
+        reg.a[P * i + e] = (r + e < r_end && col < ma) ? ld_hi(A + r + e + (int64_t)col * lda) : 0u;
     }
 #pragma unroll
-    for (int i = 0; i < Regs::kB; ++i) {
+    for (int i = 0; i < Regs::kB / P; ++i) {
       const int col = n0 + warp + kWarps * i;
-      reg.b[i] = (rin && col < mb) ? ld_hi(B + r + (int64_t)col * ldb) : 0u;
+#pragma unroll
+      for (int e = 0; e < P; ++e)
+        reg.b[P * i + e] = (r + e < r_end && col < mb) ? ld_hi(B + r + e + (int64_t)col * ldb) : 0u;
     }
   };
   auto store = [&](uint8_t* a_tile, uint8_t* b_tile, const Regs& reg) {
+    if (BF) {
 #pragma unroll
-    for (int i = 0; i < Regs::kA; ++i)
-      *reinterpret_cast<uint32_t*>(a_tile + tile_off(warp + kWarps * i, lane)) = tf32_from_hi(reg.a[i]);
+      for (int i = 0; i < Regs::kA / 2; ++i)
+        *reinterpret_cast<uint32_t*>(a_tile + tile_off_bf(warp + kWarps * i, 2 * lane)) =
+            bf16_from_hi(reg.a[2 * i]) | (bf16_from_hi(reg.a[2 * i + 1]) << 16);
 #pragma unroll
-    for (int i = 0; i < Regs::kB; ++i)
-      *reinterpret_cast<uint32_t*>(b_tile + tile_off(warp + kWarps * i, lane)) = tf32_from_hi(reg.b[i]);
+      for (int i = 0; i < Regs::kB / 2; ++i)
+        *reinterpret_cast<uint32_t*>(b_tile + tile_off_bf(warp + kWarps * i, 2 * lane)) =
+            bf16_from_hi(reg.b[2 * i]) | (bf16_from_hi(reg.b[2 * i + 1]) << 16);
+    } else {
+#pragma unroll
+      for (int i = 0; i < Regs::kA; ++i)
+        *reinterpret_cast<uint32_t*>(a_tile + tile_off(warp + kWarps * i, lane)) = tf32_from_hi(reg.a[i]);
+#pragma unroll
+      for (int i = 0; i < Regs::kB; ++i)
+        *reinterpret_cast<uint32_t*>(b_tile + tile_off(warp + kWarps * i, lane)) = tf32_from_hi(reg.b[i]);
+    }
   };
-  const bool ok = tc_mainloop<Regs, MT, NT>(nk, align_tiles(dyn), a_bytes, b_bytes, sm, tmem, idesc_tf32(kM, NT),
-                                            load, store);
+  const bool ok = tc_mainloop<Regs, MT, NT, BF>(nk, align_tiles(dyn), a_bytes, b_bytes, sm, tmem,
+                                                BF ? idesc_bf16(kM, NT) : idesc_tf32(kM, NT), load, store);
   if (ok) {
     // epilogue: warp w reads TMEM lanes 32 (w % 4).. (its quadrant) of every half, 16-column chunks w / 4, + 4, ...
     float* out = part + (int64_t)blockIdx.y * ma * mb;
@@ -274,62 +319,80 @@ __global__ void tc_reduce_kernel(const float* __restrict__ part, int nsplit, int
 
 // ------------------------------------------------------------------------------------------ Y = Y - A G / Y = A G
 // grid (ceil(n / (128 MT)), ceil(p / NT)); A: n x m, G: m x p, Y: n x p
-template <int NT, int MT>
+template <int NT, int MT, bool BF>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_update_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ G, int ldg, int64_t n, int m,
                  int p, double* Y, int64_t ldy, int subtract, int* flag) {
-  using Regs = Stage<NT, MT>;
+  using Regs = Stage<NT, MT, BF>;
+  constexpr int BK = kbk<BF>();
   extern __shared__ __align__(1024) uint8_t dyn[];
   __shared__ TcSmem sm;
   const int64_t r0 = (int64_t)blockIdx.x * kM * MT;
   const int c0 = blockIdx.y * NT;
-  const int nk = (int)ceil_div(m, kBK);
+  const int nk = (int)ceil_div(m, BK);
   constexpr uint32_t a_bytes = MT * kM * kRowB, b_bytes = (uint32_t)NT * kRowB;
   constexpr uint32_t ncols = (uint32_t)(MT * NT);
   constexpr int kRows = MT * kM;
   tc_setup(sm, ncols);
   const uint32_t tmem = sm.tmem_slot;
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
-  // A: thread items (row, 4-element chunk of k); lanes run down 32 consecutive rows of X (256 contiguous bytes per
-  // load) and each item is one 16-byte store, conflict-free under the swizzle. B (G, contiguous along k): lane = k.
+  // A: thread items (row, 16-byte chunk of k: 4 TF32 or 8 BF16 values); lanes run down 32 consecutive rows of X (256
+  // contiguous bytes per load) and each item is one 16-byte store, conflict-free under the swizzle.
+  // B (G, contiguous along k): lane = k (TF32) or the pair k = 2 lane, 2 lane + 1 (BF16).
+  constexpr int E = BF ? 8 : 4;                    // elements per 16-byte chunk
+  constexpr int P = BF ? 2 : 1;
   auto load = [&](int kb, Regs& reg) {
-    const int k0 = kb * kBK;
+    const int k0 = kb * BK;
 #pragma unroll
-    for (int i = 0; i < Regs::kA / 4; ++i) {
+    for (int i = 0; i < Regs::kA / E; ++i) {
       const int it = threadIdx.x + kThreads * i;
       const int row = it % kRows, c = it / kRows;
       const int64_t gr = r0 + row;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int gk = k0 + 4 * c + j;
-        reg.a[4 * i + j] = (gr < n && gk < m) ? ld_hi(A + gr + (int64_t)gk * lda) : 0u;
+      for (int j = 0; j < E; ++j) {
+        const int gk = k0 + E * c + j;
+        reg.a[E * i + j] = (gr < n && gk < m) ? ld_hi(A + gr + (int64_t)gk * lda) : 0u;
       }
     }
-    const int gk = k0 + lane;
+    const int gk = k0 + P * lane;
 #pragma unroll
-    for (int i = 0; i < Regs::kB; ++i) {
+    for (int i = 0; i < Regs::kB / P; ++i) {
       const int gc = c0 + warp + kWarps * i;
-      reg.b[i] = (gk < m && gc < p) ? ld_hi(G + gk + (int64_t)gc * ldg) : 0u;
+#pragma unroll
+      for (int e = 0; e < P; ++e)
+        reg.b[P * i + e] = (gk + e < m && gc < p) ? ld_hi(G + gk + e + (int64_t)gc * ldg) : 0u;
     }
   };
   auto store = [&](uint8_t* a_tile, uint8_t* b_tile, const Regs& reg) {
 #pragma unroll
-    for (int i = 0; i < Regs::kA / 4; ++i) {
+    for (int i = 0; i < Regs::kA / E; ++i) {
       const int it = threadIdx.x + kThreads * i;
       const int row = it % kRows, c = it / kRows;
       uint4 v;
-      v.x = tf32_from_hi(reg.a[4 * i + 0]);
-      v.y = tf32_from_hi(reg.a[4 * i + 1]);
-      v.z = tf32_from_hi(reg.a[4 * i + 2]);
-      v.w = tf32_from_hi(reg.a[4 * i + 3]);
-      *reinterpret_cast<uint4*>(a_tile + tile_off(row, 4 * c)) = v;
+      if (BF) {
+        v.x = bf16_from_hi(reg.a[E * i + 0]) | (bf16_from_hi(reg.a[E * i + 1]) << 16);
+        v.y = bf16_from_hi(reg.a[E * i + 2]) | (bf16_from_hi(reg.a[E * i + 3]) << 16);
+        v.z = bf16_from_hi(reg.a[E * i + 4]) | (bf16_from_hi(reg.a[E * i + 5]) << 16);
+        v.w = bf16_from_hi(reg.a[E * i + 6]) | (bf16_from_hi(reg.a[E * i + 7]) << 16);
+        *reinterpret_cast<uint4*>(a_tile + tile_off_bf(row, E * c)) = v;
+      } else {
+        v.x = tf32_from_hi(reg.a[E * i + 0]);
+        v.y = tf32_from_hi(reg.a[E * i + 1]);
+        v.z = tf32_from_hi(reg.a[E * i + 2]);
+        v.w = tf32_from_hi(reg.a[E * i + 3]);
+        *reinterpret_cast<uint4*>(a_tile + tile_off(row, E * c)) = v;
+      }
     }
 #pragma unroll
-    for (int i = 0; i < Regs::kB; ++i)
-      *reinterpret_cast<uint32_t*>(b_tile + tile_off(warp + kWarps * i, lane)) = tf32_from_hi(reg.b[i]);
+    for (int i = 0; i < Regs::kB / P; ++i) {
+      const uint32_t word = BF ? (bf16_from_hi(reg.b[2 * i]) | (bf16_from_hi(reg.b[2 * i + 1]) << 16))
+                               : tf32_from_hi(reg.b[i]);
+      *reinterpret_cast<uint32_t*>(b_tile + (BF ? tile_off_bf(warp + kWarps * i, 2 * lane)
+                                                : tile_off(warp + kWarps * i, lane))) = word;
+    }
   };
-  const bool ok = tc_mainloop<Regs, MT, NT>(nk, align_tiles(dyn), a_bytes, b_bytes, sm, tmem, idesc_tf32(kM, NT),
-                                            load, store);
+  const bool ok = tc_mainloop<Regs, MT, NT, BF>(nk, align_tiles(dyn), a_bytes, b_bytes, sm, tmem,
+                                                BF ? idesc_bf16(kM, NT) : idesc_tf32(kM, NT), load, store);
   if (ok) {
     const int q = warp & 3, h = warp >> 2;         // TMEM lane quadrant; 16-column chunks h, h + kWarps/4, ...
 #pragma unroll 1
@@ -397,75 +460,80 @@ int sm_count() {
 }
 
 
-template <int NT, int MT>
+template <int NT, int MT, bool BF>
 cudaError_t launch_gram(dim3 grid, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n, int ma,
                         int mb, int tiles_n, int64_t rows, float* part, int* flag, cudaStream_t s) {
   size_t smem = tc_smem_bytes(NT, MT);
-  cudaError_t e = set_smem((const void*)tc_gram_kernel<NT, MT>, smem, NT * MT);
+  cudaError_t e = set_smem((const void*)tc_gram_kernel<NT, MT, BF>, smem, NT * MT);
   if (e != cudaSuccess) return e;
-  tc_gram_kernel<NT, MT><<<grid, kThreads, smem, s>>>(A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag);
+  tc_gram_kernel<NT, MT, BF><<<grid, kThreads, smem, s>>>(A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag);
   count_launch();
   return cudaGetLastError();
 }
 
-template <int MT>
+template <int MT, bool BF>
 cudaError_t launch_gram_nt(int NT, dim3 grid, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n,
                            int ma, int mb, int tiles_n, int64_t rows, float* part, int* flag, cudaStream_t s) {
   switch (NT) {
-    case 32: return launch_gram<32, MT>(grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag, s);
-    case 64: return launch_gram<64, MT>(grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag, s);
-    case 128: return launch_gram<128, MT>(grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag, s);
-    default: return launch_gram<256, MT>(grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag, s);
+    case 32: return launch_gram<32, MT, BF>(grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag, s);
+    case 64: return launch_gram<64, MT, BF>(grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag, s);
+    case 128: return launch_gram<128, MT, BF>(grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag, s);
+    default: return launch_gram<256, MT, BF>(grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, part, flag, s);
   }
 }
 
-template <int NT, int MT>
+template <int NT, int MT, bool BF>
 cudaError_t launch_update(const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p, double* Y,
                           int64_t ldy, bool subtract, int* flag, cudaStream_t s) {
   size_t smem = tc_smem_bytes(NT, MT);
-  cudaError_t e = set_smem((const void*)tc_update_kernel<NT, MT>, smem, NT * MT);
+  cudaError_t e = set_smem((const void*)tc_update_kernel<NT, MT, BF>, smem, NT * MT);
   if (e != cudaSuccess) return e;
-  tc_update_kernel<NT, MT><<<dim3((unsigned)ceil_div(n, (int64_t)kM * MT), (unsigned)ceil_div(p, NT)), kThreads, smem,
-                             s>>>(A, lda, G, ldg, n, m, p, Y, ldy, subtract ? 1 : 0, flag);
+  tc_update_kernel<NT, MT, BF><<<dim3((unsigned)ceil_div(n, (int64_t)kM * MT), (unsigned)ceil_div(p, NT)), kThreads,
+                                 smem, s>>>(A, lda, G, ldg, n, m, p, Y, ldy, subtract ? 1 : 0, flag);
   count_launch();
   return cudaGetLastError();
 }
 
-template <int MT>
+template <int MT, bool BF>
 cudaError_t launch_update_nt(int NT, const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p,
                              double* Y, int64_t ldy, bool subtract, int* flag, cudaStream_t s) {
   switch (NT) {
-    case 32: return launch_update<32, MT>(A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
-    case 64: return launch_update<64, MT>(A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
-    case 128: return launch_update<128, MT>(A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
-    default: return launch_update<256, MT>(A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
+    case 32: return launch_update<32, MT, BF>(A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
+    case 64: return launch_update<64, MT, BF>(A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
+    case 128: return launch_update<128, MT, BF>(A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
+    default: return launch_update<256, MT, BF>(A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
   }
 }
 
 }  // namespace
 
 cudaError_t tc_gram(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n, int ma, int mb, double* C,
-                    int ldc, bool symmetric, double* part, size_t part_capacity, int* flag, cudaStream_t s) {
+                    int ldc, bool symmetric, double* part, size_t part_capacity, int* flag, cudaStream_t s, bool bf16) {
   if (ma <= 0 || mb <= 0) return cudaSuccess;
   if ((size_t)ma * mb > part_capacity) return cudaErrorInvalidValue;
-  const int NT = pick_nt(mb);
-  const int MT = ma > kM ? 2 : 1;                  // two accumulators share each converted B tile
+  // BF16 stages twice as many K values per tile row, so its register staging keeps one 128-row accumulator and at
+  // most 128 columns
+  const int NT = bf16 ? std::min(pick_nt(mb), 128) : pick_nt(mb);
+  const int MT = (!bf16 && ma > kM) ? 2 : 1;       // two accumulators share each converted B tile
+  const int BK = bf16 ? kbk<true>() : kbk<false>();
   const int tiles_m = (int)ceil_div(ma, kM * MT), tiles_n = (int)ceil_div(mb, NT);
   const int tiles = tiles_m * tiles_n;
   // one wave of CTAs, while the FP32 partials (written, then read by the reduce; mostly L2-resident) stay below
   // half of the input bytes
   int64_t nsplit = ceil_div((int64_t)sm_count(), tiles);
   const int64_t cap_traffic = (n * (int64_t)(ma + mb)) / (2LL * ma * mb) + 1;
-  const int64_t cap_rows = ceil_div(n, 4 * kBK);
+  const int64_t cap_rows = ceil_div(n, 4 * BK);
   const int64_t cap_mem = (int64_t)(2 * part_capacity / ((size_t)ma * mb));   // FP32 partials in FP64 space
   nsplit = std::min(nsplit, std::min(cap_traffic, std::min(cap_rows, cap_mem)));
   if (nsplit < 1) nsplit = 1;
-  const int64_t rows = ceil_div(ceil_div(n, nsplit), kBK) * kBK;
+  const int64_t rows = ceil_div(ceil_div(n, nsplit), BK) * BK;
   const int nsp = (int)ceil_div(n, rows);
   const dim3 grid(tiles, nsp);
   float* fpart = reinterpret_cast<float*>(part);     // FP32 partials in the FP64 partial buffer (half its bytes)
-  cudaError_t e = MT == 2 ? launch_gram_nt<2>(NT, grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, fpart, flag, s)
-                          : launch_gram_nt<1>(NT, grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, fpart, flag, s);
+  cudaError_t e;
+  if (bf16) e = launch_gram_nt<1, true>(NT, grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, fpart, flag, s);
+  else if (MT == 2) e = launch_gram_nt<2, false>(NT, grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, fpart, flag, s);
+  else e = launch_gram_nt<1, false>(NT, grid, A, lda, B, ldb, n, ma, mb, tiles_n, rows, fpart, flag, s);
   if (e != cudaSuccess) return e;
   const int64_t blocks = ceil_div((int64_t)ma * mb, 256);
   tc_reduce_kernel<<<(unsigned)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(fpart, nsp, ma, mb, C, ldc,
@@ -475,13 +543,15 @@ cudaError_t tc_gram(const double* A, int64_t lda, const double* B, int64_t ldb, 
 }
 
 cudaError_t tc_update(const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p, double* Y,
-                      int64_t ldy, bool subtract, int* flag, cudaStream_t s) {
+                      int64_t ldy, bool subtract, int* flag, cudaStream_t s, bool bf16) {
   if (p <= 0 || n <= 0) return cudaSuccess;
+  if (bf16) return launch_update_nt<1, true>(std::min(pick_nt(p), 128), A, lda, G, ldg, n, m, p, Y, ldy, subtract,
+                                             flag, s);
   const int NT = pick_nt(p);
   // 256-row tiles (two accumulators sharing each converted G tile) unless that leaves more than half the SMs idle
   const bool two = 2 * ceil_div(n, (int64_t)2 * kM) * ceil_div(p, NT) >= sm_count();
-  return two ? launch_update_nt<2>(NT, A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s)
-             : launch_update_nt<1>(NT, A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
+  return two ? launch_update_nt<2, false>(NT, A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s)
+             : launch_update_nt<1, false>(NT, A, lda, G, ldg, n, m, p, Y, ldy, subtract, flag, s);
 }
 
 }  // namespace ppcg

@@ -19,12 +19,12 @@ template <bool RESID>
 __global__ void __launch_bounds__(256)
 precond_kernel(const double* __restrict__ X, const double* __restrict__ HX, double* W, int64_t ld, int64_t n, int m,
                const double* __restrict__ lam, const double* __restrict__ dg, double sigma, double delta,
-               double* __restrict__ norm_part) {
+               const double* __restrict__ tinvp, double* __restrict__ norm_part) {
   const int r_loc = threadIdx.x % kRows;
   const int c_loc = threadIdx.x / kRows;          // 4 column lanes; columns c0 + c_loc + 4 j
   const int64_t r = (int64_t)blockIdx.x * kRows + r_loc;
   const int c0 = blockIdx.y * 4 * kColsPerThread;
-  const double tinv = r < n ? 1.0 / fmax(dg[r] - sigma, delta) : 0.0;
+  const double tinv = r < n ? (tinvp ? tinvp[r] : 1.0 / fmax(dg[r] - sigma, delta)) : 0.0;
   double sq[kColsPerThread];
 #pragma unroll
   for (int j = 0; j < kColsPerThread; ++j) {
@@ -284,6 +284,55 @@ cudaError_t locked_gram_fill(double* G, double* M, int m, int kl, const double* 
   return cudaGetLastError();
 }
 
+// Gs = G_aa - T (ka x ka, leading dimension ka; G_aa read from the k_t x k_t Gram at offset kl); a Schur pivot
+// Gs_ii below pivot_tol^2 G_aa,ii (the active column nearly inside the span of the locked ones) flags a breakdown
+__global__ void locked_schur_kernel(const double* __restrict__ G, int kt, int kl, const double* __restrict__ T,
+                                    double pivot_tol, double* __restrict__ Gs, int* flag) {
+  const int ka = kt - kl;
+  const int64_t cnt = (int64_t)ka * ka;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % ka), j = (int)(e / ka);
+    const double g = G[(kl + i) + (int64_t)(kl + j) * kt];
+    const double v = g - T[e];
+    Gs[e] = v;
+    if (i == j && !(v >= pivot_tol * pivot_tol * g)) atomicOr(flag, kFlagCholBreakdown);
+  }
+}
+
+// R^{-1} of G = [[I, G_la], [G_la^T, G_aa]] from U = G_la Ra^{-1} and Ra^{-1} (Ra^T Ra = G_aa - G_la^T G_la):
+// R^{-1} = [[I, -U], [0, Ra^{-1}]] (k_t x k_t, leading dimension k_t)
+__global__ void locked_rinv_fill_kernel(double* __restrict__ Rinv, int kt, int kl, const double* __restrict__ U,
+                                        const double* __restrict__ Rainv) {
+  const int ka = kt - kl;
+  const int64_t cnt = (int64_t)kt * kt;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % kt), j = (int)(e / kt);
+    double v;
+    if (j < kl) v = (i == j) ? 1.0 : 0.0;
+    else if (i < kl) v = -U[i + (int64_t)(j - kl) * kl];
+    else v = Rainv[(i - kl) + (int64_t)(j - kl) * ka];
+    Rinv[e] = v;
+  }
+}
+
+cudaError_t locked_schur(const double* G, int kt, int kl, const double* T, double pivot_tol, double* Gs, int* flag,
+                         cudaStream_t s) {
+  const int64_t cnt = (int64_t)(kt - kl) * (kt - kl);
+  const int64_t b = ceil_div(cnt, 256);
+  locked_schur_kernel<<<(unsigned)(b < 4096 ? (b < 1 ? 1 : b) : 4096), 256, 0, s>>>(G, kt, kl, T, pivot_tol, Gs,
+                                                                                   flag);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t locked_rinv_fill(double* Rinv, int kt, int kl, const double* U, const double* Rainv, cudaStream_t s) {
+  const int64_t cnt = (int64_t)kt * kt;
+  const int64_t b = ceil_div(cnt, 256);
+  locked_rinv_fill_kernel<<<(unsigned)(b < 4096 ? b : 4096), 256, 0, s>>>(Rinv, kt, kl, U, Rainv);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t eye_residual(double* G, int m, double* fro2, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
   eye_residual_kernel<<<1, 1024, 0, s>>>(G, m, fro2);
@@ -310,7 +359,8 @@ cudaError_t residual_diag(const double* X, const double* HX, int64_t ld, int64_t
                           const ResidualArgs& ra, double* W, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
   dim3 grid((unsigned)norm_row_tiles(n), (unsigned)ceil_div(m, 4 * kColsPerThread));
-  precond_kernel<true><<<grid, 256, 0, s>>>(X, HX, W, ld, n, m, lam, ra.dg, ra.sigma, ra.delta, ra.norm_part);
+  precond_kernel<true><<<grid, 256, 0, s>>>(X, HX, W, ld, n, m, lam, ra.dg, ra.sigma, ra.delta, ra.tinv,
+                                            ra.norm_part);
   count_launch();
   return cudaGetLastError();
 }
@@ -319,7 +369,20 @@ cudaError_t precond_norms(double* W, int64_t ld, int64_t n, int m, const Residua
   if (m <= 0) return cudaSuccess;
   dim3 grid((unsigned)norm_row_tiles(n), (unsigned)ceil_div(m, 4 * kColsPerThread));
   precond_kernel<false><<<grid, 256, 0, s>>>(nullptr, nullptr, W, ld, n, m, nullptr, ra.dg, ra.sigma, ra.delta,
-                                             ra.norm_part);
+                                             ra.tinv, ra.norm_part);
+  count_launch();
+  return cudaGetLastError();
+}
+
+__global__ void precond_diag_kernel(const double* __restrict__ dg, double sigma, double delta, int64_t n,
+                                    double* __restrict__ tinv) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    tinv[r] = 1.0 / fmax(dg[r] - sigma, delta);
+}
+
+cudaError_t precond_diag(const double* dg, double sigma, double delta, int64_t n, double* tinv, cudaStream_t s) {
+  const int64_t b = ceil_div(n, 256);
+  precond_diag_kernel<<<(unsigned)(b < 4096 ? b : 4096), 256, 0, s>>>(dg, sigma, delta, n, tinv);
   count_launch();
   return cudaGetLastError();
 }

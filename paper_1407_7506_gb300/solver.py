@@ -46,7 +46,7 @@ class Solver:
         self.opt.no_lock = 0 if lock else 1
         self.opt.timing = 1 if timing else 0
         self.opt.sigma_floor = sigma_floor
-        self.opt.precision = {"fp64": 0, "mixed_tf32": 1, "mixed": 1}[precision]
+        self.opt.precision = {"fp64": 0, "mixed_tf32": 1, "mixed": 1, "mixed_bf16": 2}[precision]
         self.opt.fp64_gemm = {"fma": 0, "ozaki": 1}[fp64_gemm]
         self.opt.orth = {"cholqr2": 0, "polar": 1}[orth]
         self.opt.orth_skip_tol = orth_skip_tol

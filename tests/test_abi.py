@@ -112,9 +112,12 @@ def test_unsupported_options_are_reported(lib):
     op.theta[1] = 0.5                                   # a Bloch twist needs the complex dtype
     assert lib.ppcg_workspace_bytes(ctypes.byref(op), 4096, 8, 2, None, ctypes.byref(out)) == pk.PPCG_ERR_UNSUPPORTED
     opt = pk.ppcg_options()
-    opt.precision = 2                                   # BF16 mixed form: not provided
+    opt.precision = 3                                   # no such precision
     assert (lib.ppcg_workspace_bytes(ctypes.byref(_op(16)), 4096, 8, 2, ctypes.byref(opt), ctypes.byref(out))
             == pk.PPCG_ERR_UNSUPPORTED)
+    opt.precision = 2                                   # the BF16 mixed form is provided
+    assert (lib.ppcg_workspace_bytes(ctypes.byref(_op(16)), 4096, 8, 2, ctypes.byref(opt), ctypes.byref(out))
+            == pk.PPCG_OK)
 
 
 def test_null_handles_and_pointers(lib):

@@ -438,6 +438,53 @@ def test_project_tensor_core_tf32(N, mx, my):
     assert np.max(np.abs(X.T @ Z)) < 50 * U_TF32 * np.max(np.abs(Y)) * np.sqrt(n)
 
 
+# ------------------------------------------------------------------------------------- mixed form: tcgen05 BF16
+U_BF16 = 2.0 ** -8           # unit roundoff of BF16 (7 explicit mantissa bits, round to nearest)
+
+
+@pytest.mark.parametrize("N,ma,mb,sym", [(5, 37, 61, False), (10, 70, 130, False), (16, 256, 256, False),
+                                         (16, 130, 130, True), (16, 200, 33, False), (10, 1, 1, False),
+                                         (30, 300, 260, False), (32, 256, 256, True)])
+def test_gram_tensor_core_bf16(N, ma, mb, sym):
+    # kind::f16 with BF16 operands (converted from FP64 on load, round to nearest) and FP32 accumulation
+    n = N ** 3
+    rng = _rng(ma * 1000 + mb + 9)
+    A = rng.standard_normal((n, ma))
+    B = A if sym else rng.standard_normal((n, mb))
+    with Handle(np.zeros(n), N, kt=max(ma, mb), sbsize=1, precision=2) as H:
+        Ad = dev(A)
+        Bd = Ad if sym else dev(B)
+        Cd = torch.empty((mb, ma), dtype=torch.float64, device="cuda")
+        pk.ppcg_gram(H.h, ptr(Ad), n, ptr(Bd), n, ma, mb, ptr(Cd))
+        C = host(Cd)
+    ref = A.T @ B
+    # each product carries two BF16 roundings; the FP32 accumulation adds far less
+    bound = (2.2 * U_BF16 + 1e-5) * (np.abs(A).T @ np.abs(B))
+    assert np.all(np.abs(C - ref) <= bound), np.max(np.abs(C - ref) / bound)
+    assert np.max(np.abs(C - ref) / bound) > 1e-3      # the BF16 rounding is really there
+    if sym:
+        np.testing.assert_array_equal(C, C.T)
+
+
+@pytest.mark.parametrize("N,mx,my", [(10, 17, 5), (16, 64, 64), (30, 300, 260), (32, 256, 1)])
+def test_project_tensor_core_bf16(N, mx, my):
+    n = N ** 3
+    rng = _rng(mx + my + 1)
+    X = oracle.cholqr2(rng.standard_normal((n, mx)))[0]
+    Y = rng.standard_normal((n, my))
+    with Handle(np.zeros(n), N, kt=max(mx, my), sbsize=1, precision=2) as H:
+        Xd, Yd = dev(X), dev(Y)
+        pk.ppcg_project(H.h, ptr(Xd), n, mx, ptr(Yd), n, my)
+        Z = host(Yd)
+    ref = oracle.project(Y, X)
+    # G = X^T Y has BF16 errors ~ 2u |X|^T |Y|; W - X G adds ~ 2u |X| |G|
+    G_abs = np.abs(X).T @ np.abs(Y)
+    bound = 2.2 * U_BF16 * (np.abs(X) @ G_abs) * 2 + 1e-12
+    assert np.all(np.abs(Z - ref) <= bound)
+    # the projection still removes span(X) up to the BF16 level
+    assert np.max(np.abs(X.T @ Z)) < 50 * U_BF16 * np.max(np.abs(Y)) * np.sqrt(n)
+
+
 # ------------------------------------------------------------------------------------- FP64 emulation (Ozaki)
 @pytest.mark.parametrize("N,ma,mb,sym,spread", [(5, 37, 61, False, 0), (10, 70, 130, False, 30),
                                                 (16, 256, 256, False, 0), (16, 130, 130, True, 20),

@@ -120,29 +120,32 @@ def test_iteration_history_tracks_oracle(N, k, q):
 LAM_TOL_MIXED = 1e-9
 
 
+@pytest.mark.parametrize("precision", ["mixed", "mixed_bf16"])
 @pytest.mark.parametrize("N,k,q", [(8, 8, 2), (10, 20, 6), (9, 12, 3)])
-def test_mixed_form_solve(N, k, q):
-    # TF32 projections and first CholQR Gram on the tensor cores; every pair still reaches residual 1e-8
+def test_mixed_form_solve(N, k, q, precision):
+    # TF32 or BF16 projections and first CholQR Gram on the tensor cores; every pair still reaches residual 1e-8
     w = wl.small("mx", N=N, k=k, sbsize=q, seed=70 + N + k)
     V, X0 = wl.make_inputs(w)
-    lam, X, res, st = _gpu_solve(V, N, k, q, 5, X0, precision="mixed")
+    lam, X, res, st = _gpu_solve(V, N, k, q, 5, X0, precision=precision)
     assert st["status"] == "ok" and st["converged"] == 1, st
     _check_pairs(V, N, lam, X, 1e-8)
     ev = np.linalg.eigvalsh(oracle.assemble_H(V, N, 1.0))[:k]
     assert np.all(_rel(lam, ev) <= LAM_TOL_MIXED), np.max(_rel(lam, ev))
 
 
-def test_mixed_form_grid16_k64_against_dense_golden():
+@pytest.mark.parametrize("precision", ["mixed", "mixed_bf16"])
+def test_mixed_form_grid16_k64_against_dense_golden(precision):
     w = wl.GRID16_K64
     V, X0 = wl.make_inputs(w)
     gold = np.loadtxt(os.path.join(GOLDEN, "grid16_k64_dense_eigs.txt"))[:w.k]
-    lam, X, res, st = _gpu_solve(V, w.N, w.k, w.sbsize, w.rr_period, X0, tol=w.tol, maxiter=5000, precision="mixed")
+    lam, X, res, st = _gpu_solve(V, w.N, w.k, w.sbsize, w.rr_period, X0, tol=w.tol, maxiter=5000,
+                                 precision=precision)
     assert st["converged"] == 1, st
     assert np.all(_rel(lam, gold) <= LAM_TOL_MIXED), np.max(_rel(lam, gold))
     _check_pairs(V, w.N, lam, X, w.tol)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_bf16"])
 def test_fp64_emulation_solve_grid16_k64(precision):
     # every FP64 n x k GEMM on the tensor cores (error-free splitting): the FP64-form bars still hold
     w = wl.GRID16_K64
@@ -231,8 +234,9 @@ def test_solve_grid32_k256_full_size():
 
 
 @pytest.mark.slow
-def test_grid48_k1024_mixed_form_against_separable_spectrum():
-    # the 48^3, k = 1024 shape and form (sbsize = 8, TF32 projections, FP64-accurate GEMMs otherwise)
+@pytest.mark.parametrize("precision", ["mixed", "mixed_bf16"])
+def test_grid48_k1024_mixed_form_against_separable_spectrum(precision):
+    # the 48^3, k = 1024 shape and form (sbsize = 8, TF32 or BF16 projections, FP64-accurate GEMMs otherwise)
     # with a separable potential, whose spectrum is known exactly: sums of three 1-D spectra
     N, k, q = 48, 1024, 8
     w = wl.small("sep48", N=N, k=k, sbsize=q, potential="separable", seed=1003)
@@ -243,7 +247,7 @@ def test_grid48_k1024_mixed_form_against_separable_spectrum():
     L = 2 * np.eye(N) - np.roll(np.eye(N), 1, 0) - np.roll(np.eye(N), -1, 0)      # periodic 1-D second difference
     mus = [np.linalg.eigvalsh(L + np.diag(v)) for v in (v1, v2, v3)]
     exact = np.sort((mus[0][:, None, None] + mus[1][None, :, None] + mus[2][None, None, :]).ravel())[:k + 1]
-    lam, X, res, st = _gpu_solve(V, N, k, q, 5, X0, precision="mixed", fp64_gemm="ozaki", maxiter=4000)
+    lam, X, res, st = _gpu_solve(V, N, k, q, 5, X0, precision=precision, fp64_gemm="ozaki", maxiter=4000)
     assert st["status"] == "ok" and st["converged"] == 1, st
     assert np.all(_rel(lam, exact[:k]) <= 1e-9), np.max(_rel(lam, exact[:k]))
     cols = np.random.default_rng(1).choice(k, 32, replace=False)
