@@ -253,7 +253,20 @@ def oracle_trajectory(history, kt):
 # runs of iterations [first, last] with the same number of active columns, and the Rayleigh-Ritz iterations, as the
 # library's solve history recorded them (bench.py prints them as "trajectory"). The main arm uses the trajectory
 # of its own timed solve instead.
-TRAJECTORY_GRID48 = None
+TRAJECTORY_GRID48 = {
+    "runs": [(1, 25, 1024), (26, 30, 1020), (31, 35, 890), (36, 40, 756), (41, 45, 648), (46, 50, 538), (51, 55, 455),
+             (56, 60, 402), (61, 65, 354), (66, 70, 306), (71, 75, 272), (76, 80, 241), (81, 85, 220), (86, 90, 192),
+             (91, 95, 179), (96, 100, 162), (101, 105, 152), (106, 110, 138), (111, 115, 131), (116, 120, 117),
+             (121, 125, 114), (126, 130, 107), (131, 135, 100), (136, 140, 90), (141, 145, 86), (146, 150, 81),
+             (151, 155, 79), (156, 160, 73), (161, 165, 71), (166, 170, 69), (171, 175, 63), (176, 180, 59),
+             (181, 185, 55), (186, 190, 51), (191, 195, 50), (196, 200, 46), (201, 210, 43), (211, 215, 40),
+             (216, 220, 37), (221, 225, 31), (226, 230, 30), (231, 245, 28), (246, 250, 26), (251, 255, 23),
+             (256, 260, 22), (261, 265, 21), (266, 275, 20), (276, 280, 19), (281, 285, 18), (286, 295, 17),
+             (296, 305, 16), (306, 310, 15), (311, 320, 14), (321, 325, 12), (326, 330, 11), (331, 340, 10),
+             (341, 355, 9), (356, 365, 6), (366, 410, 5), (411, 440, 4), (441, 550, 3), (551, 690, 2), (691, 1209, 1),
+             (1209, 1209, 1)],
+    "rr": sorted(set(range(5, 1210, 5)) | {1209}),
+}
 
 
 def trajectory_summary(traj):
@@ -269,6 +282,17 @@ def trajectory_summary(traj):
         else:
             runs.append([int(it), int(it), int(ka)])
     return {"runs": runs, "rr": rr}
+
+
+def convergence_summary(history, samples=24):
+    """Max Ritz residual, active columns and elapsed time at a spread of the solve's Rayleigh-Ritz steps (the
+    residual-versus-time view of the paper's Figure "Liband")."""
+    rr = [r for r in history if int(r[1]) == 1]
+    if not rr:
+        return []
+    pick = sorted(set(np.linspace(0, len(rr) - 1, min(samples, len(rr))).round().astype(int).tolist()))
+    return [{"iter": int(rr[i][0]), "t_ms": round(float(rr[i][5]), 1), "max_res": float(rr[i][2]),
+             "k_act": int(rr[i][4])} for i in pick]
 
 
 def trajectory_expand(summary, kt):
@@ -355,7 +379,10 @@ def workload_config(w, form):
                           else "V ~ U[0,1)"),
             "operator": (f"complex Bloch twist {w.theta}, solved in the real form of order 2n"
                          if w.dtype == "c128" else "real symmetric"),
-            "l2": f"no flush: working set {7 * w.n * w.k * 8 / 2**20:.0f} MiB > {L2_BYTES // 2**20} MiB L2"}
+            "l2": (f"no flush: working set {7 * w.n * w.k * 8 / 2**20:.0f} MiB > {L2_BYTES // 2**20} MiB L2"
+                   if 7 * w.n * w.k * 8 > L2_BYTES else
+                   f"no flush: working set {7 * w.n * w.k * 8 / 2**20:.0f} MiB fits the {L2_BYTES // 2**20} MiB L2; "
+                   "every pass of the solve reuses it, as the method does")}
 
 
 # form name -> (precision, how the FP64 n x k GEMMs run, step-18 orthonormalisation)
@@ -403,6 +430,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-separable", action="store_true")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="only the roofline timings of the hot kernels at the workload's shape (for profiling)")
     ap.add_argument("--batch-concurrency", type=int, default=16, help="concurrent solves of the batched workload")
     ap.add_argument("--batch-gemm", default="fma", choices=["fma", "ozaki"],
                     help="FP64 GEMMs of the batched workload: FP64 FMA pipe or Ozaki emulation on tcgen05")
@@ -439,6 +468,9 @@ def main():
     gold = stored_eigs(w)
     cplx = w.dtype == "c128"
     sk = {"dtype": w.dtype, "theta": w.theta} if cplx else {}          # Solver arguments of the operator
+    if args.kernels_only:
+        print(json.dumps(rooflines(pk, w, dev, stream, V_d, sk)), flush=True)
+        return 0
 
     def solver(form, **kw):
         prec, gm, orth = FORMS[form]
@@ -547,6 +579,7 @@ def main():
                    "counts": f["counts"]}
             for name, f in results.items()},
         "window_forms": windows,
+        "convergence": convergence_summary(head["history"]),
         "trajectory": trajectory_summary(traj),
     }
     print(json.dumps(line), flush=True)

@@ -75,10 +75,12 @@ typedef struct {
   double sigma_floor;   /* [0 -> 0.1/h^2] floor delta of the preconditioner diagonal, see ppcg_solve */
   int32_t timing;       /* [0] 1 records per-phase device times into ppcg_stats.t_phase_ms */
   int32_t history_cap;  /* [0] capacity (entries) of history */
-  double* history;      /* [NULL] host array of 5 * history_cap doubles; entry i = {iteration, kind,
-                           value, trace, k_act}: kind 0 = plain step (value = ||W||_F over the wanted columns),
-                           kind 1 = Rayleigh-Ritz step (value = max_i r_i, trace = sum of the k Ritz values);
-                           k_act = active (unlocked) columns the iteration worked on (k + nbuf for iteration 0) */
+  double* history;      /* [NULL] host array of 6 * history_cap doubles; entry i = {iteration, kind,
+                           value, trace, k_act, t_ms}: kind 0 = plain step (value = ||W||_F over the wanted
+                           columns), kind 1 = Rayleigh-Ritz step (value = max_i r_i, trace = sum of the k Ritz
+                           values); k_act = active (unlocked) columns the iteration worked on (k + nbuf for
+                           iteration 0); t_ms = milliseconds since the solve began, taken when the step's norms
+                           reached the host */
   int32_t fp64_gemm;    /* [0] how the FP64 n x k GEMMs run: 0 = FP64 FMA pipe, 1 = FP64-accurate emulation on
                            the BF16 tensor cores (error-free splitting into 8 digit slices, Ozaki scheme) */
   int32_t orth;         /* [0] step 18 (Section 5.5): 0 = CholeskyQR2; 1 = polar X <- X (X^T X)^{-1/2} by the

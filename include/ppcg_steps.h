@@ -40,10 +40,14 @@ PPCG_API ppcg_status ppcg_cholqr2(ppcg_handle h, double* X, int64_t ldx, int32_t
 /* Symmetric eigensolver of the Rayleigh-Ritz step (steps 23-24, Section 5.6): M is m x m (leading dimension m,
  * the upper triangle is read), lambda receives the m eigenvalues ascending and C (m x m) the orthonormal
  * eigenvectors as columns. M, lambda and C are device buffers owned by the caller; C must not overlap M.
- * Route: if no off-diagonal entry exceeds 1e-14 ||M||_F, the sorted diagonal and unit vectors. If none exceeds
- * 1e-6 ||M||_F, eigenvector refinement from the identity (Ogita and Aishima 2018), accepted once every correction
- * is <= 1e-8, with Rayleigh-quotient eigenvalues. Otherwise, or if refinement does not settle within 4 steps,
- * parallel cyclic Jacobi. Synchronises the stream; returns PPCG_ERR_TIMEOUT if a bounded device wait gave up. */
+ * Routes, cheapest first: if no off-diagonal entry exceeds 1e-14 ||M||_F, the sorted diagonal and unit vectors.
+ * If none exceeds 1e-4 ||M||_F, eigenvector refinement from the identity (Ogita and Aishima 2018), with clusters of
+ * close eigenvalues solved as small eigenproblems; otherwise (or if that does not settle within 4 steps) the same
+ * refinement started from the eigenvectors of a single-precision parallel Jacobi. A refinement is accepted once
+ * every correction is <= 1e-8 and no cluster pair couples above 1e-14 ||M||_F; its eigenvalues are the Rayleigh
+ * quotients of the final vectors. Parallel FP64 Jacobi is the fallback. The m x m products run on the FP64
+ * tensor-core emulation when the handle was created with fp64_gemm = 1. Synchronises the stream; returns
+ * PPCG_ERR_TIMEOUT if a bounded device wait gave up. */
 PPCG_API ppcg_status ppcg_dense_eigh(ppcg_handle h, const double* M, int32_t m, double* lambda, double* C);
 
 /* Steps 11-13 (eq. projev on S_j = [X_j, W_j, P_j], Section 5.1): for each of the s = ceil(k_act/q) sub-blocks

@@ -71,6 +71,7 @@ struct ppcg_ctx {
   bool cplx = false;       // complex Hermitian (Bloch) problem, solved in the real form of order 2 ng
   int64_t ng = 0;          // grid points (the complex order); n = 2 ng for a complex handle
   int kc = 0;              // wanted complex pairs (k = 2 kc internally)
+  std::chrono::steady_clock::time_point t_solve0;   // start of the current solve (history time stamps)
 };
 
 namespace {
@@ -601,12 +602,15 @@ ppcg_status rr_step(ppcg_ctx* c, SolveState& st, bool allow_compact, ppcg_stats*
 
 void record(ppcg_ctx* c, ppcg_stats* S, int it, int kind, double value, double trace, int k_act) {
   if (!c->opt.history || S->history_len >= c->opt.history_cap) return;
-  double* e = c->opt.history + 5 * (size_t)S->history_len;
+  double* e = c->opt.history + 6 * (size_t)S->history_len;
   e[0] = it;
   e[1] = kind;
   e[2] = value;
   e[3] = trace;
   e[4] = k_act;
+  // every entry is recorded right after the stream was synchronised to read the step's norms: host time since the
+  // solve began is the device's progress (the residual-versus-time view of the paper's Figure "Liband")
+  e[5] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - c->t_solve0).count();
   S->history_len++;
 }
 
@@ -765,6 +769,7 @@ ppcg_status ppcg_solve(ppcg_handle c, const double* X0, double tol, double* lamb
   ppcg_stats local{};
   ppcg_stats* S = stats ? stats : &local;
   std::memset(S, 0, sizeof(*S));
+  c->t_solve0 = std::chrono::steady_clock::now();
   c->eig_count[0] = c->eig_count[1] = c->eig_count[2] = c->eig_count[3] = 0;
   std::memset(c->t_ms, 0, sizeof(c->t_ms));
   c->evused = 0;

@@ -1052,11 +1052,11 @@ cudaError_t jacobi_eigh(const double* M, int m, double* lambda, double* C, doubl
 // in a solve is nearly diagonal in the basis of the previous Ritz vectors, and then the parallel Jacobi method still
 // pays its full rounds of grid barriers. (1) If no off-diagonal entry exceeds kJacobiTol ||M||_F (the Jacobi stop
 // test), the eigenpairs are the sorted diagonal and unit vectors. (2) If none exceeds kRefineTau ||M||_F, the
-// eigenvectors are refined from the identity (see the refinement kernels above). (3) Otherwise a single-precision
-// Jacobi, whose rotations run on the wide FP32 pipe, gives eigenvectors accurate to about 1e-6, and the refinement
-// takes them to FP64 accuracy in two or three steps of m x m products. (4) If a refinement does not settle within
-// kRefineSteps steps, or a cluster exceeds kMaxCluster values, FP64 Jacobi on M. Accepted refinements take the
-// Rayleigh quotients of the final vectors as eigenvalues.
+// eigenvectors are refined from the identity (see the refinement kernels above). (3) Otherwise, or if (2) does not
+// settle, a single-precision Jacobi, whose rotations run on the wide FP32 pipe, gives eigenvectors accurate to about
+// 1e-6, and the refinement takes them to FP64 accuracy in two or three steps of m x m products. (4) If that does not
+// settle within kRefineSteps steps, or a cluster exceeds kMaxCluster values, FP64 Jacobi on M. Accepted refinements
+// take the Rayleigh quotients of the final vectors as eigenvalues.
 // msym: m x m scratch (not aliasing M or C) for the symmetrised M.
 cudaError_t dense_eigh_auto(const double* Min, int m, double* lambda, double* C, double* ws, double* msym,
                             const KxK& g, int* flag, unsigned* bar, int* sweeps_out_dev, int* path_out,
@@ -1085,8 +1085,64 @@ cudaError_t dense_eigh_auto(const double* Min, int m, double* lambda, double* C,
     *path_out = 1;
     return cudaGetLastError();
   }
-  const bool from_identity = off <= kRefineTau * nM;
-  if (!from_identity) {
+  const int64_t cnt = (int64_t)m * m;
+  const unsigned gcl = (unsigned)ceil_div(m, 2);
+  // kRefineSteps refinement steps from Z = I (from_identity) or from the Z the FP32 Jacobi left in w.Z; returns
+  // 1 when a step was accepted (outputs written), 0 when not, -1 on a CUDA error (in e)
+  auto refine = [&](bool from_identity) -> int {
+    for (int t = 0; t < kRefineSteps; ++t) {
+      const double* St = M;
+      const double* Gt = nullptr;
+      if (t > 0 || !from_identity) {
+        if ((e = kxk_gemm(g, true, w.Z, m, w.Z, m, m, m, m, G, m, s)) != cudaSuccess) return -1;      // Z^T Z
+        if ((e = kxk_gemm(g, true, M, m, w.Z, m, m, m, m, w.T, m, s)) != cudaSuccess) return -1;      // M Z
+        if ((e = kxk_gemm(g, true, w.Z, m, w.T, m, m, m, m, w.S, m, s)) != cudaSuccess) return -1;    // Z^T M Z
+        St = w.S;
+        Gt = G;
+      }
+      refine_diag_kernel<<<1, 1024, 0, s>>>(St, Gt, m, w.lam, w.stat);
+      refine_coupling_kernel<<<grid_for(cnt), 256, 0, s>>>(St, Gt, m, w.lam, w.stat);
+      rank_sort_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(w.lam, 1, m, w.lam + w.mp, w.order);
+      refine_cluster_kernel<<<1, 1024, 0, s>>>(w.lam + w.mp, w.order, m, w.stat, w.cid, w.cls, w.cln);
+      refine_coef_kernel<<<grid_for(cnt), 256, 0, s>>>(St, Gt, m, w.lam, w.cid, thr, w.stat, w.E);
+      refine_cluster_eig_kernel<<<gcl, 256, 0, s>>>(St, Gt, m, w.lam, w.order, w.cls, w.cln, w.stat, w.E);
+      count_launch(6);
+      if (t == 0 && from_identity) {
+        identity_plus_kernel<<<grid_for(cnt), 256, 0, s>>>(w.E, m, w.Z);
+        count_launch();
+      } else {
+        if ((e = kxk_gemm(g, false, w.Z, m, w.E, m, m, m, m, w.T, m, s)) != cudaSuccess) return -1;   // Z E
+        add_kernel<<<grid_for(cnt), 256, 0, s>>>(w.T, cnt, w.Z);
+        count_launch();
+      }
+      if ((e = cudaMemcpyAsync(h + 2, w.stat + 2, 5 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return -1;
+      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return -1;
+      if (h[6] != 0.0) return 0;                              // a cluster too large for shared memory
+      if (h[2] <= kRefineAccept && h[3] <= thr) {
+        if ((e = kxk_gemm(g, true, M, m, w.Z, m, m, m, m, w.T, m, s)) != cudaSuccess) return -1;    // M Z
+        rayleigh_quotient_kernel<<<(unsigned)ceil_div(m, 8), 256, 0, s>>>(w.Z, w.T, m, w.lam);
+        count_launch();
+        rank_sort_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(w.lam, 1, m, lambda, w.perm);
+        count_launch();
+        gather_perm_kernel<<<grid_for(cnt), 256, 0, s>>>(w.Z, m, w.perm, C);
+        count_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return -1;
+        return 1;
+      }
+      if (!(h[2] <= 1.0)) return 0;                           // diverging: corrections of order one
+    }
+    return 0;
+  };
+  if (off <= kRefineTau * nM) {
+    const int r = refine(true);
+    if (r < 0) return e;
+    if (r > 0) {
+      *path_out = 2;
+      return cudaSuccess;
+    }
+  }
+  {
     // single-precision Jacobi for the starting vectors
     const JacBuf<float> jb = jac_buffers<float>(w);
     e = run_jacobi<float>(M, m, w, jb, kJacobiTol32, kJacobiMaxSweeps32, flag, bar, sweeps_out_dev, s);
@@ -1094,48 +1150,11 @@ cudaError_t dense_eigh_auto(const double* Min, int m, double* lambda, double* C,
     jacobi32_to_z_kernel<<<grid_for((int64_t)m * m), 256, 0, s>>>(jb, m, w.mp, sweeps_out_dev, w.Z);
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  const int64_t cnt = (int64_t)m * m;
-  const unsigned gcl = (unsigned)ceil_div(m, 2);
-  for (int t = 0; t < kRefineSteps; ++t) {
-    const double* St = M;
-    const double* Gt = nullptr;
-    if (t > 0 || !from_identity) {
-      if ((e = kxk_gemm(g, true, w.Z, m, w.Z, m, m, m, m, G, m, s)) != cudaSuccess) return e;        // Z^T Z
-      if ((e = kxk_gemm(g, true, M, m, w.Z, m, m, m, m, w.T, m, s)) != cudaSuccess) return e;        // M Z
-      if ((e = kxk_gemm(g, true, w.Z, m, w.T, m, m, m, m, w.S, m, s)) != cudaSuccess) return e;      // Z^T M Z
-      St = w.S;
-      Gt = G;
-    }
-    refine_diag_kernel<<<1, 1024, 0, s>>>(St, Gt, m, w.lam, w.stat);
-    refine_coupling_kernel<<<grid_for(cnt), 256, 0, s>>>(St, Gt, m, w.lam, w.stat);
-    rank_sort_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(w.lam, 1, m, w.lam + w.mp, w.order);
-    refine_cluster_kernel<<<1, 1024, 0, s>>>(w.lam + w.mp, w.order, m, w.stat, w.cid, w.cls, w.cln);
-    refine_coef_kernel<<<grid_for(cnt), 256, 0, s>>>(St, Gt, m, w.lam, w.cid, thr, w.stat, w.E);
-    refine_cluster_eig_kernel<<<gcl, 256, 0, s>>>(St, Gt, m, w.lam, w.order, w.cls, w.cln, w.stat, w.E);
-    count_launch(6);
-    if (t == 0 && from_identity) {
-      identity_plus_kernel<<<grid_for(cnt), 256, 0, s>>>(w.E, m, w.Z);
-      count_launch();
-    } else {
-      if ((e = kxk_gemm(g, false, w.Z, m, w.E, m, m, m, m, w.T, m, s)) != cudaSuccess) return e;     // Z E
-      add_kernel<<<grid_for(cnt), 256, 0, s>>>(w.T, cnt, w.Z);
-      count_launch();
-    }
-    if ((e = cudaMemcpyAsync(h + 2, w.stat + 2, 5 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-      return e;
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-    if (h[6] != 0.0) break;                                   // a cluster too large for shared memory
-    if (h[2] <= kRefineAccept && h[3] <= thr) {
-      if ((e = kxk_gemm(g, true, M, m, w.Z, m, m, m, m, w.T, m, s)) != cudaSuccess) return e;        // M Z
-      rayleigh_quotient_kernel<<<(unsigned)ceil_div(m, 8), 256, 0, s>>>(w.Z, w.T, m, w.lam);
-      count_launch();
-      rank_sort_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(w.lam, 1, m, lambda, w.perm);
-      count_launch();
-      gather_perm_kernel<<<grid_for(cnt), 256, 0, s>>>(w.Z, m, w.perm, C);
-      count_launch();
-      *path_out = from_identity ? 2 : 3;
-      return cudaGetLastError();
+    const int r = refine(false);
+    if (r < 0) return e;
+    if (r > 0) {
+      *path_out = 3;
+      return cudaSuccess;
     }
   }
   return jacobi_eigh(Min, m, lambda, C, ws, flag, bar, sweeps_out_dev, s);

@@ -16,7 +16,7 @@ constexpr double kJacobiTol = 1e-14;    // k x k Jacobi: rotate while |a_pq| > k
                                         // left below that adds < ~1e-12 to a Ritz residual (tol is 1e-8)
 constexpr double kJacobiTolSmall = 1e-16;  // sub-block warp Jacobi
 constexpr int kJacobiMaxSweeps = 60;
-constexpr double kRefineTau = 1e-6;      // refine from the identity when max |M_ij| (i != j) <= kRefineTau ||M||_F
+constexpr double kRefineTau = 1e-4;      // refine from the identity when max |M_ij| (i != j) <= kRefineTau ||M||_F
 constexpr int kRefineSteps = 4;          // refinement steps before falling back to Jacobi
 constexpr double kRefineAccept = 1e-8;   // accept a refinement step whose largest |E_ij| (i != j) is at most this
 constexpr double kJacobiTol32 = 3e-7;    // single-precision Jacobi (start of the refinement): rotate while

@@ -50,7 +50,7 @@ class Solver:
         self.opt.fp64_gemm = {"fma": 0, "ozaki": 1}[fp64_gemm]
         self.opt.orth = {"cholqr2": 0, "polar": 1}[orth]
         self.opt.orth_skip_tol = orth_skip_tol
-        self._hist = np.zeros(5 * max(history, 1))
+        self._hist = np.zeros(6 * max(history, 1))
         if history:
             self.opt.history_cap = history
             self.opt.history = self._hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -79,7 +79,7 @@ class Solver:
         status = ppcg_solve(self.handle, X0t.data_ptr(), tol, lam.ctypes.data, X.data_ptr(), res.ctypes.data, st)
         d = st.as_dict()
         d["status"] = "ok" if status == PPCG_OK else ("not_converged" if status == PPCG_ERR_NOT_CONVERGED else status)
-        d["history"] = self._hist[:5 * d["history_len"]].reshape(-1, 5).copy()
+        d["history"] = self._hist[:6 * d["history_len"]].reshape(-1, 6).copy()
         return lam, X, res, d
 
     def close(self):

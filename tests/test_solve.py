@@ -115,6 +115,7 @@ def test_iteration_history_tracks_oracle(N, k, q):
     np.testing.assert_allclose(g[:early][tr, 3], o[:early][tr, 3], rtol=1e-12)
     # active columns per iteration: all k at first, never growing (locking only removes columns)
     assert g[0, 4] == k and np.all(np.diff(g[:, 4]) <= 0) and np.all(g[:, 4] >= 1)
+    assert g[0, 5] > 0 and np.all(np.diff(g[:, 5]) >= 0)          # time stamps: increasing
 
 
 LAM_TOL_MIXED = 1e-9
