@@ -46,7 +46,7 @@ METRIC = "time-to-tol 1e-8 and PPCG iters/s, mixed vs FP64 form on 1 GB300; % ro
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12          # 1.2586, at the 2070 MHz maximum SM clock
 L2_BYTES = 129 * 2 ** 20
 WORKLOADS = {"grid48_k1024": wl.GRID48_K1024, "grid32_k256": wl.GRID32_K256, "grid16_k64": wl.GRID16_K64,
-             "grid32_k128_bloch": wl.GRID32_K128_BLOCH}
+             "grid32_k128_bloch": wl.GRID32_K128_BLOCH, "grid48_k512_bloch": wl.GRID48_K512_BLOCH}
 
 
 def _env_rank():
@@ -418,7 +418,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="grid48_k1024", choices=list(WORKLOADS) + ["batch64"],
                     help="grid48_k1024 (default: the mixed-form workload), grid32_k256, grid16_k64, "
-                         "grid32_k128_bloch (the complex Bloch recipe), batch64 (64 uneven problems)")
+                         "grid48_k512_bloch, grid32_k128_bloch (the complex Bloch recipe), batch64 (64 uneven "
+                         "problems)")
     ap.add_argument("--maxiter", type=int, default=6000)
     ap.add_argument("--forms", default="mixed_ozaki,fp64_ozaki,mixed_bf16_ozaki",
                     help="forms solved to tolerance; the first is the headline value (" + ", ".join(FORMS) + ")")
@@ -553,7 +554,7 @@ def main():
     head = results[first]
     traj = [(int(r[0]), int(r[1]), int(r[4])) for r in head["history"]]
     roofs = rooflines(pk, w, dev, stream, V_d, sk)
-    sep = None if args.no_separable else separable_parity(pk, w, dev, stream, first, args.maxiter)
+    sep = None if (args.no_separable or cplx) else separable_parity(pk, w, dev, stream, first, args.maxiter)
     e2e = None if args.no_e2e else run_e2e(pk, w, V, X0, max(1, args.e2e_steps), stream, FORMS[first])
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

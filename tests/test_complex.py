@@ -129,6 +129,51 @@ def test_complex_energy_gradient_and_finite_differences():
         s.close()
 
 
+@pytest.mark.slow
+def test_complex_gradient_central_differences_32_entries_at_16cubed():
+    # the Bloch recipe (twist theta, Gaussian wells) at 16^3 with k = 16: the adjoint dE/dV = sum_i |x_i|^2 against
+    # dense eigenvectors, and against central differences (step 1e-5) on 32 random potential entries, each from two
+    # solves warm-started at the returned vectors with tol 1e-10, differencing the eigenvalues pair by pair
+    N, k, q = 16, 16, 4
+    w = wl.small("c5fd", N=N, k=k, sbsize=q, potential="wells", n_wells=4, seed=1005, dtype="c128", theta=THETA)
+    V, X0 = wl.make_inputs(w)
+    n = N ** 3
+    ev, U = np.linalg.eigh(oracle.assemble_H(V, N, 1.0, THETA))
+    assert ev[k] - ev[k - 1] > 1e-3                     # a gap above lambda_k: E is differentiable
+    s = pk.Solver(V, N, k, q, rr_period=5, maxiter=4000, dtype="c128", theta=THETA, fp64_gemm="ozaki")
+    try:
+        Vt = torch.tensor(V, device="cuda", requires_grad=True)
+        E = pk.smallest_eigsum(Vt, s, X0, tol=1e-10)
+        E.backward()
+        g = Vt.grad.cpu().numpy()
+        np.testing.assert_allclose(float(E.detach()), np.sum(ev[:k]), rtol=1e-12)
+        np.testing.assert_allclose(np.sum(g), k, rtol=1e-12)          # sum_p dE/dV_p = k for unit vectors
+        ref = oracle.energy_gradient(U[:, :k])
+        scale = np.maximum(np.abs(ref), k / n)
+        assert np.max(np.abs(g - ref) / scale) <= 1e-8
+        _, X, _, _ = s.solve(X0, 1e-10)
+        Xw = np.asfortranarray(X.cpu().numpy().T)
+        # At step 1e-5 the difference quotient carries the eigenvalues' own rounding (a few ulps of ||A|| each,
+        # divided by the step): even dense LAPACK eigenvalues give errors of several 1e-6 relative on some entries
+        # here. So the step-1e-5 quotients are held to 1e-6 relative plus that rounding bound, and quotients at
+        # step 1e-4 (truncation error ~1e-7 relative, rounding ten times smaller) to 1e-6 relative alone.
+        norm_a = 12.0 + np.max(np.abs(V))
+        for p in np.random.default_rng(11).choice(n, 32, replace=False):
+            scale = max(abs(g[p]), k / n)
+            for hstep, slack in ((1e-5, k * 4 * np.finfo(float).eps / 2 * norm_a / 1e-5), (1e-4, 0.0)):
+                e = np.zeros(n)
+                e[p] = hstep
+                s.set_potential(torch.tensor(V + e, device="cuda"))
+                lp, _, _, sp = s.solve(Xw, 1e-10)
+                s.set_potential(torch.tensor(V - e, device="cuda"))
+                lm, _, _, sm = s.solve(Xw, 1e-10)
+                assert sp["converged"] == 1 and sm["converged"] == 1
+                fd = np.sum((lp - lm) / (2 * hstep))
+                assert abs(fd - g[p]) <= 1e-6 * scale + slack, (p, hstep, fd, g[p])
+    finally:
+        s.close()
+
+
 def test_bloch_wells_recipe_at_12cubed():
     # the 64^3 Bloch recipe (64 wells on a Bloch-twisted grid) scaled to 12^3, k = 24, sbsize = 4
     w = wl.small("c5s", N=12, k=24, sbsize=4, potential="wells", n_wells=8, seed=1005, dtype="c128", theta=THETA)

@@ -51,13 +51,16 @@ class Workload:
 
 # The workloads of the method's benchmark set: plain FP64 at two sizes, the mixed form at 48^3, and the complex
 # Bloch recipe (its full 64^3, k = 2048 size does not converge within a benchmark run on one GPU, so it is also
-# defined at the largest size that does: 32^3 with k = 128). The batched set is batch() below.
+# defined at smaller sizes: 48^3 with k = 512 and 32^3 with k = 128). The batched set is batch() below.
 GRID16_K64 = Workload("grid16_k64_q1_uniform", N=16, k=64, sbsize=1, potential="uniform", seed=1001)
 GRID32_K256 = Workload("grid32_k256_q4_wells8", N=32, k=256, sbsize=4, potential="wells", n_wells=8, seed=1002)
 GRID48_K1024 = Workload("grid48_k1024_q8_wells32", N=48, k=1024, sbsize=8, potential="wells", n_wells=32,
                         seed=1003, precision="mixed")
 GRID64_K2048_BLOCH = Workload("grid64_k2048_q8_wells64_bloch", N=64, k=2048, sbsize=8, potential="wells",
                               n_wells=64, seed=1005, dtype="c128", theta=(0.3, 0.7, 1.1))
+# the Bloch recipe at 48^3 with k = 512 and sbsize = 8: the wells keep the 64^3 recipe's density (64 x (48/64)^3 = 27)
+GRID48_K512_BLOCH = Workload("grid48_k512_q8_wells27_bloch", N=48, k=512, sbsize=8, potential="wells", n_wells=27,
+                             seed=1005, dtype="c128", theta=(0.3, 0.7, 1.1))
 GRID32_K128_BLOCH = Workload("grid32_k128_q4_wells8_bloch", N=32, k=128, sbsize=4, potential="wells", n_wells=8,
                              seed=1005, dtype="c128", theta=(0.3, 0.7, 1.1))
 
