@@ -487,20 +487,25 @@ oz_update_kernel(const double* __restrict__ A, int64_t lda, const double* __rest
 }
 
 // ------------------------------------------------------------------------------------------ pre-sliced Grams
-// The Gram's operands are sliced once, by a streaming kernel, into "digit images": for every TW-column tile t
-// (TW = 128 for the A role, 64 for the B role) and every 16-row block b of the operand, 8 planes (one per digit),
-// each the exact shared-memory image of a TW-row x 16-K operand tile in the canonical K-major layout (core
-// matrices of 8 rows x 16 bytes; 128 B between core matrices along K, 256 B between 8-row groups). The 8 planes of
-// a (t, b) pair are contiguous, so one bulk asynchronous copy (cp.async.bulk) per operand and stage moves them into
-// shared memory, through a 4-deep mbarrier pipeline: no digit arithmetic sits in the Gram's main loop and every
-// operand element is sliced once instead of once per output tile.
+// The Gram's operands are sliced once, by a streaming kernel, into "digit images": for every 128-column tile t and
+// every 16-row block b of the operand, 8 planes (one per digit), each the exact shared-memory image of a 128-row x
+// 16-K operand tile in the canonical K-major layout (core matrices of 8 rows x 16 bytes; 128 B between core matrices
+// along K, 256 B between 8-row groups). The 8 planes of a (t, b) pair are contiguous, so one bulk asynchronous copy
+// (cp.async.bulk) per operand and stage moves them into shared memory through an mbarrier ring: no digit arithmetic
+// sits in the product's main loop and every operand element is sliced once instead of once per output tile.
+//
+// Output tiles are 128 x 128. The 8 group accumulators of a 128 x 128 tile would need 1024 TMEM columns, so the
+// product runs every exact-accumulation chunk twice: pass 0 accumulates groups g = 0..3 (digit planes 0..3 of
+// both operands), pass 1 groups g = 4..7 (all planes), each in 4 accumulators of 128 columns (all 512 TMEM
+// columns), and each pass is folded at the chunk's end. Against 128 x 64 tiles with all 8 groups resident, every
+// MMA is twice as wide, so the tensor cores read half as many operand bytes from shared memory per product.
 constexpr int kSK = 16;                                   // K per stage
 constexpr uint32_t kSSBO = (kSK / 8) * 128;              // 256 B between 8-row groups
-constexpr uint32_t kSImg = (64 / 8) * kSSBO;             // 2 KB: one 64-row plane
-constexpr uint32_t kSAPlane = 2 * kSImg;                 // 128 rows
-constexpr uint32_t kSBPlane = kSImg;                     // 64 rows
-constexpr uint32_t kSStage = kDig * (kSAPlane + kSBPlane);   // 48 KB
-constexpr int kSBuf = 4;
+constexpr uint32_t kSAPlane = (128 / 8) * kSSBO;         // 4 KB: one 128-row plane
+constexpr uint32_t kImgBlk = kDig * kSAPlane;            // 32 KB: the 8 planes of one (tile, 16-row block)
+constexpr uint32_t kStage2 = 2 * kImgBlk;                // 64 KB: both operands, all planes
+constexpr int kSBuf = 3;
+constexpr int kN2 = 128;                                 // output columns per tile of the image-fed product
 constexpr int kSChunkBlocks = kChunk / kSK;             // 32 stages per exact-accumulation chunk
 
 __device__ __forceinline__ uint32_t tile_off16(int row, int k) {
@@ -544,7 +549,7 @@ struct OzImgSmem {
   int ok;
   int issued, consumed;
   int Ea[kM];
-  int Eb[kN];
+  int Eb[kN2];
 };
 
 // Image-fed product. Gram (UPD = false): out = the split's FP64 partial of A^T B (ma x mb, leading dimension ma),
@@ -564,19 +569,42 @@ struct ImgArgs {
   int* flag;
 };
 
+// fold the 4 accumulators of pass p (groups 4 p .. 4 p + 3) of this warp's 32 lanes x 64 columns into (hi, lo)
+__device__ __forceinline__ void fold_pass(uint32_t tmem, int q, int h, int pass, float (&hi)[64], float (&lo)[64]) {
+#pragma unroll 1
+  for (int gl = 3; gl >= 0; --gl) {
+    const int g = 4 * pass + gl;
+    const float w = __int_as_float((127 - 7 * g) << 23);   // 2^(-7 g), exact
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(gl * kN2 + 64 * h + 32 * c), v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const float x = v[i] * w;
+        const float sm = hi[32 * c + i] + x;
+        const float bb = sm - hi[32 * c + i];
+        lo[32 * c + i] += (hi[32 * c + i] - (sm - bb)) + (x - bb);
+        hi[32 * c + i] = sm;
+      }
+    }
+  }
+}
+
 template <bool UPD>
 __global__ void __launch_bounds__(kThreads, 1) oz_img_kernel(ImgArgs a) {
   extern __shared__ __align__(1024) uint8_t dyn[];
   __shared__ OzImgSmem sm;
   const int tm = blockIdx.x / a.tiles_n, tn = blockIdx.x % a.tiles_n;
-  const int m0 = tm * kM, n0 = tn * kN;
-  if (!UPD && a.symmetric && n0 + kN <= m0) return;   // entirely below the diagonal: the reduce reads only i <= j
+  const int m0 = tm * kM, n0 = tn * kN2;
+  if (!UPD && a.symmetric && n0 + kN2 <= m0) return;   // entirely below the diagonal: the reduce reads only i <= j
   const int kb0 = blockIdx.y * a.kb_per_split;
   const int kb1 = min(a.nkb, kb0 + a.kb_per_split);
   const int nst = kb1 > kb0 ? kb1 - kb0 : 0;
+  const int nit = 2 * nst;                        // stage items: every stage once per pass
   const int tid = threadIdx.x;
   for (int i = tid; i < kM; i += kThreads) sm.Ea[i] = (m0 + i < a.ma) ? a.Ea[m0 + i] : kNoExp;
-  for (int i = tid; i < kN; i += kThreads) sm.Eb[i] = (n0 + i < a.mb) ? a.Eb[n0 + i] : kNoExp;
+  for (int i = tid; i < kN2; i += kThreads) sm.Eb[i] = (n0 + i < a.mb) ? a.Eb[n0 + i] : kNoExp;
   if (tid == 0) {
     for (int b = 0; b < kSBuf; ++b) {
       mbar_init(smem_u32(&sm.full[b]), 1);
@@ -595,72 +623,89 @@ __global__ void __launch_bounds__(kThreads, 1) oz_img_kernel(ImgArgs a) {
   const uint32_t tmem = sm.tmem_slot;
   const int warp = tid / 32, lane = tid & 31;
   const int q = warp & 3, h = warp >> 2;
-  const uint8_t* srcA = a.imgA + (size_t)tm * a.nkb * kDig * kSAPlane;
-  const uint8_t* srcB = a.imgB + (size_t)tn * a.nkb * kDig * kSBPlane;
-  // Thread 0 of warp 0 produces (bulk copies into a free buffer), thread 0 of warp 1 consumes (MMAs, then a commit
-  // that frees the buffer); both run ahead independently within a chunk of kSChunkBlocks stages, and all warps meet
-  // at the chunk end to fold the group accumulators. issued / consumed live in shared memory for the timeout path.
-  auto issue = [&](int st) {                      // both operands of stage st into buffer st % kSBuf
-    const int b = st % kSBuf;
-    const uint32_t dst = smem_u32(dyn + b * kSStage);
-    const uint32_t fb = smem_u32(&sm.full[b]);
-    mbar_expect_tx(fb, kSStage);
-    bulk_g2s(dst, srcA + (size_t)(kb0 + st) * kDig * kSAPlane, kDig * kSAPlane, fb);
-    bulk_g2s(dst + kDig * kSAPlane, srcB + (size_t)(kb0 + st) * kDig * kSBPlane, kDig * kSBPlane, fb);
+  const uint8_t* srcA = a.imgA + (size_t)tm * a.nkb * kImgBlk;
+  const uint8_t* srcB = a.imgB + (size_t)tn * a.nkb * kImgBlk;
+  // Item t is (pass, stage) of chunk t / (2 CB): the chunk's len stages in pass 0, then the same stages in pass 1
+  // (CB = kSChunkBlocks; the last chunk may be shorter). Pass 0 needs digit planes 0..3 of both operands, pass 1 all
+  // 8. Thread 0 of warp 0 produces (bulk copies into a free buffer), thread 0 of warp 1 consumes (MMAs, then a
+  // commit that frees the buffer); both run ahead independently within a (chunk, pass) block, and all warps meet at
+  // its end to fold its 4 group accumulators. issued / consumed live in shared memory for the timeout path.
+  auto item = [&](int t, int& pass, int& st) {
+    const int ci = t / (2 * kSChunkBlocks);
+    const int c0 = ci * kSChunkBlocks;
+    const int len = min(kSChunkBlocks, nst - c0);
+    const int r = t - 2 * kSChunkBlocks * ci;
+    pass = r >= len ? 1 : 0;
+    st = c0 + r - pass * len;
   };
-  float hi[32], lo[32];
+  auto issue = [&](int t) {                       // item t into buffer t % kSBuf
+    int pass, st;
+    item(t, pass, st);
+    const int b = t % kSBuf;
+    const uint32_t dst = smem_u32(dyn + b * kStage2);
+    const uint32_t fb = smem_u32(&sm.full[b]);
+    const uint32_t bytes = pass ? kImgBlk : kImgBlk / 2;      // planes 0..7 or 0..3 of each operand
+    mbar_expect_tx(fb, 2 * bytes);
+    bulk_g2s(dst, srcA + (size_t)(kb0 + st) * kImgBlk, bytes, fb);
+    bulk_g2s(dst + kImgBlk, srcB + (size_t)(kb0 + st) * kImgBlk, bytes, fb);
+  };
+  float hi[64], lo[64];
 #pragma unroll
-  for (int i = 0; i < 32; ++i) { hi[i] = 0.f; lo[i] = 0.f; }
-  constexpr uint32_t idesc = idesc_bf16(kM, kN);
+  for (int i = 0; i < 64; ++i) { hi[i] = 0.f; lo[i] = 0.f; }
+  constexpr uint32_t idesc = idesc_bf16(kM, kN2);
   bool ok = true;
   int issued = 0, consumed = 0;                   // thread 0 / thread 32 only
-  for (int c0 = 0; c0 < nst; c0 += kSChunkBlocks) {
-    const int c1 = min(nst, c0 + kSChunkBlocks);
-    if (tid == 0) {
-      // keep up to kSBuf stages in flight: this chunk's and the first ones of the next
-      const int upto = min(nst, c1 + kSBuf - 1);
-      for (int st = issued; st < upto && sm.ok; ++st) {
-        if (st >= kSBuf && !mbar_wait(smem_u32(&sm.empty[st % kSBuf]), (uint32_t)((st / kSBuf - 1) & 1))) {
-          sm.ok = 0;
-          break;
-        }
-        issue(st);
-        issued = st + 1;
-        sm.issued = issued;
-      }
-    } else if (tid == 32) {
-      for (int st = c0; st < c1 && sm.ok; ++st) {
-        const int b = st % kSBuf;
-        if (!mbar_wait(smem_u32(&sm.full[b]), (uint32_t)((st / kSBuf) & 1))) {
-          sm.ok = 0;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t a0 = smem_u32(dyn + b * kSStage), b0 = a0 + kDig * kSAPlane;
-        const bool first = st == c0;
-#pragma unroll
-        for (int g = 0; g < kGroups; ++g) {
-#pragma unroll
-          for (int j = 0; j <= g; ++j) {
-            mma_bf16(tmem + (uint32_t)(g * kN), smem_desc_nosw(a0 + j * kSAPlane, 128, kSSBO),
-                     smem_desc_nosw(b0 + (g - j) * kSBPlane, 128, kSSBO), idesc, (first && j == 0) ? 0u : 1u);
+  const int nchunk = (int)ceil_div(nst, kSChunkBlocks);
+  for (int ci = 0; ci < nchunk && ok; ++ci) {
+    const int len = min(kSChunkBlocks, nst - ci * kSChunkBlocks);
+    for (int pass = 0; pass < 2; ++pass) {
+      const int tb0 = 2 * kSChunkBlocks * ci + pass * len, tb1 = tb0 + len;
+      if (tid == 0) {
+        // keep up to kSBuf items in flight: this block's and the first ones of the next
+        const int upto = min(nit, tb1 + kSBuf - 1);
+        for (int t = issued; t < upto && sm.ok; ++t) {
+          if (t >= kSBuf && !mbar_wait(smem_u32(&sm.empty[t % kSBuf]), (uint32_t)((t / kSBuf - 1) & 1))) {
+            sm.ok = 0;
+            break;
           }
+          issue(t);
+          issued = t + 1;
+          sm.issued = issued;
         }
-        mma_commit(smem_u32(&sm.empty[b]));
-        consumed = st + 1;
-        sm.consumed = consumed;
+      } else if (tid == 32) {
+        for (int t = tb0; t < tb1 && sm.ok; ++t) {
+          const int b = t % kSBuf;
+          if (!mbar_wait(smem_u32(&sm.full[b]), (uint32_t)((t / kSBuf) & 1))) {
+            sm.ok = 0;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(dyn + b * kStage2), b0 = a0 + kImgBlk;
+          const bool first = t == tb0;
+#pragma unroll
+          for (int gl = 0; gl < 4; ++gl) {
+            const int g = 4 * pass + gl;
+            for (int j = 0; j <= g; ++j) {           // digit pairs (j, g - j), both at most 7 since g <= 7
+              mma_bf16(tmem + (uint32_t)(gl * kN2), smem_desc_nosw(a0 + j * kSAPlane, 128, kSSBO),
+                       smem_desc_nosw(b0 + (g - j) * kSAPlane, 128, kSSBO), idesc, (first && j == 0) ? 0u : 1u);
+            }
+          }
+          mma_commit(smem_u32(&sm.empty[b]));
+          consumed = t + 1;
+          sm.consumed = consumed;
+        }
+        // the block's products are complete once its last commit has arrived
+        if (sm.ok && consumed == tb1 &&
+            !mbar_wait(smem_u32(&sm.empty[(tb1 - 1) % kSBuf]), (uint32_t)(((tb1 - 1) / kSBuf) & 1)))
+          sm.ok = 0;
       }
-      // the chunk's products are complete once its last commit has arrived
-      if (sm.ok && consumed == c1 &&
-          !mbar_wait(smem_u32(&sm.empty[(c1 - 1) % kSBuf]), (uint32_t)(((c1 - 1) / kSBuf) & 1)))
-        sm.ok = 0;
+      __syncthreads();
+      if (!sm.ok) { ok = false; break; }
+      tc_fence_after();
+      fold_pass(tmem, q, h, pass, hi, lo);
+      tc_fence_before();
+      __syncthreads();
     }
-    __syncthreads();
-    if (!sm.ok) { ok = false; break; }
-    tc_fence_after();
-    fold_groups(tmem, q, h, hi, lo);
-    tc_fence_before();
-    __syncthreads();
   }
   if (ok) {
     const int ri = 32 * q + lane;
@@ -669,23 +714,16 @@ __global__ void __launch_bounds__(kThreads, 1) oz_img_kernel(ImgArgs a) {
       const int Ei = sm.Ea[ri];
       double* row = UPD ? a.out + gi : a.out + (int64_t)blockIdx.y * a.ma * a.mb + gi;
       const int64_t ld = UPD ? a.ldo : a.ma;
-      double yv[32];
-      if (UPD && a.mode != (int)Epi::Store) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int gj = n0 + 32 * h + i;
-          yv[i] = gj < a.mb ? row[(int64_t)gj * ld] : 0.0;
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int cj = 32 * h + i;
+      for (int i = 0; i < 64; ++i) {            // fully unrolled: hi / lo stay in registers
+        const int cj = 64 * h + i;
         const int gj = n0 + cj;
         if (gj >= a.mb) continue;
         const int Ej = sm.Eb[cj];
         const double v = (nst == 0 || Ei == kNoExp || Ej == kNoExp) ? 0.0
                                                                     : (widen(hi[i]) + widen(lo[i])) * pow2(Ei + Ej - 10);
-        row[(int64_t)gj * ld] = (UPD && a.mode != (int)Epi::Store) ? yv[i] - v : v;
+        double* o = row + (int64_t)gj * ld;
+        *o = (UPD && a.mode != (int)Epi::Store) ? *o - v : v;
       }
     }
   }
@@ -693,8 +731,8 @@ __global__ void __launch_bounds__(kThreads, 1) oz_img_kernel(ImgArgs a) {
     atomicOr(a.flag, kFlagTimeout);
     // wait (bounded) for the copies and MMAs still in flight before the CTA gives its memory back
     const int iss = sm.issued, con = sm.consumed;
-    for (int st = con; st < iss; ++st)
-      mbar_wait(smem_u32(&sm.full[st % kSBuf]), (uint32_t)((st / kSBuf) & 1));
+    for (int t = con; t < iss; ++t)
+      mbar_wait(smem_u32(&sm.full[t % kSBuf]), (uint32_t)((t / kSBuf) & 1));
     if (con > 0) mbar_wait(smem_u32(&sm.empty[(con - 1) % kSBuf]), (uint32_t)(((con - 1) / kSBuf) & 1));
   }
   tc_fence_before();
@@ -732,7 +770,7 @@ oz_slice_rows_kernel(const double* __restrict__ M, int64_t ld, int64_t nrows, in
   }
 }
 
-size_t oz_img_smem() { return (size_t)kSBuf * kSStage + 1024; }
+size_t oz_img_smem() { return (size_t)kSBuf * kStage2 + 1024; }
 
 size_t oz_smem() { return 2 * (size_t)kStageBytes + 1024; }
 
@@ -772,9 +810,9 @@ cudaError_t prep_img(const void* fn) {
   return per_sm <= 1 ? cudaSuccess : cudaErrorInvalidConfiguration;
 }
 
-size_t oz_img_bytes(int64_t n, int cols) {   // one A-role (128-column tiles) plus one B-role (64-column) image
+size_t oz_img_bytes(int64_t n, int cols) {   // the images of both operands (128-column tiles each)
   const size_t nkb = (size_t)ceil_div(n, kSK);
-  return ((size_t)ceil_div(cols, 128) * kSAPlane + (size_t)ceil_div(cols, 64) * kSBPlane) * nkb * kDig;
+  return 2 * (size_t)ceil_div(cols, 128) * kImgBlk * nkb;
 }
 
 cudaError_t oz_gram(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n, int ma, int mb, double* C,
@@ -796,28 +834,44 @@ cudaError_t oz_gram(const double* A, int64_t lda, const double* B, int64_t ldb, 
   const int tiles_m = (int)ceil_div(ma, kM), tiles_n = (int)ceil_div(mb, kN);
   const int tiles = tiles_m * tiles_n;
   const int64_t nkb64 = ceil_div(n, kSK);
-  const size_t bytesA = (size_t)ceil_div(ma, 128) * kSAPlane * kDig * nkb64;
-  const size_t bytesB = (size_t)ceil_div(mb, 64) * kSBPlane * kDig * nkb64;
-  if (img && img_bytes >= bytesA + bytesB && tiles_n >= 2) {
+  const size_t bytesA = (size_t)ceil_div(ma, 128) * kImgBlk * nkb64;
+  const size_t bytesB = (size_t)ceil_div(mb, 128) * kImgBlk * nkb64;
+  if (img && img_bytes >= bytesA + bytesB && mb > kN) {
     // several column tiles of B would each re-slice A: slice each operand once into digit images instead, then
-    // run the bulk-copy-fed Gram
+    // run the bulk-copy-fed Gram on 128 x 128 tiles
     const int nkb = (int)ceil_div(n, kSK);
+    const int tiles_n2 = (int)ceil_div(mb, kN2);
+    const int tiles2 = tiles_m * tiles_n2;
     uint8_t* imgA = img;
     uint8_t* imgB = img + bytesA;
     oz_slice_kernel<128><<<(unsigned)(ceil_div(ma, 128) * nkb), 256, 0, s>>>(A, lda, n, ma, Ea, imgA, nkb);
-    oz_slice_kernel<64><<<(unsigned)(ceil_div(mb, 64) * nkb), 256, 0, s>>>(B, ldb, n, mb, Eb, imgB, nkb);
+    oz_slice_kernel<128><<<(unsigned)(ceil_div(mb, 128) * nkb), 256, 0, s>>>(B, ldb, n, mb, Eb, imgB, nkb);
     count_launch(2);
     const size_t smem = oz_img_smem();
     cudaError_t e = prep_img((const void*)oz_img_kernel<false>);
     if (e != cudaSuccess) return e;
-    int64_t nsplit = ceil_div(sm_count(), tiles);
-    const int64_t cap_rows = ceil_div(nkb, kSChunkBlocks);
-    const int64_t cap_mem = (int64_t)(part_capacity / ((size_t)ma * mb));
-    nsplit = std::max<int64_t>(1, std::min(nsplit, std::min(cap_rows, cap_mem)));
-    const int kps = (int)(ceil_div(ceil_div(nkb, nsplit), kSChunkBlocks) * kSChunkBlocks);
+    // CTAs that do work (a symmetric Gram skips the tiles below the diagonal); the K split, in whole chunks, is the
+    // one with the fewest waves x chunks per CTA (one CTA per SM), the smaller split on ties
+    int64_t active = tiles2;
+    if (symmetric && ma == mb) active = (int64_t)tiles_m * (tiles_m + 1) / 2;
+    const int64_t nchunks = ceil_div(nkb, kSChunkBlocks);
+    const int64_t cap_mem = std::max<int64_t>(1, (int64_t)(part_capacity / ((size_t)ma * mb)));
+    const int64_t sms = sm_count();
+    int64_t cps = nchunks;                        // chunks per split
+    int64_t best = ceil_div(active, sms) * nchunks;
+    for (int64_t c = nchunks - 1; c >= 1; --c) {
+      const int64_t ns = ceil_div(nchunks, c);
+      if (ns > cap_mem) break;
+      const int64_t cost = ceil_div(active * ns, sms) * c;
+      if (cost < best) {
+        best = cost;
+        cps = c;
+      }
+    }
+    const int kps = (int)(cps * kSChunkBlocks);
     const int nsp = (int)ceil_div(nkb, kps);
-    const ImgArgs args{imgA, imgB, nkb, ma, mb, tiles_n, kps, Ea, Eb, part, ma, symmetric ? 1 : 0, 0, flag};
-    oz_img_kernel<false><<<dim3(tiles, nsp), kThreads, smem, s>>>(args);
+    const ImgArgs args{imgA, imgB, nkb, ma, mb, tiles_n2, kps, Ea, Eb, part, ma, symmetric ? 1 : 0, 0, flag};
+    oz_img_kernel<false><<<dim3(tiles2, nsp), kThreads, smem, s>>>(args);
     count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -848,17 +902,17 @@ cudaError_t oz_update(const double* A, int64_t lda, const double* G, int ldg, in
   if (e != cudaSuccess) return e;
   e = col_exps(G, ldg, m, p, Fc, s);
   if (e != cudaSuccess) return e;
-  const int tiles_m = (int)ceil_div(n, kM), tiles_n = (int)ceil_div(p, kN);
+  const int tiles_m = (int)ceil_div(n, kM), tiles_n = (int)ceil_div(p, kN2);
   const int nkb = (int)ceil_div(m, kSK);
-  const size_t bytesA = (size_t)tiles_m * nkb * kDig * kSAPlane;
-  const size_t bytesB = (size_t)tiles_n * nkb * kDig * kSBPlane;
-  if (img && img_bytes >= bytesA + bytesB && tiles_n >= 2) {
+  const size_t bytesA = (size_t)tiles_m * nkb * kImgBlk;
+  const size_t bytesB = (size_t)tiles_n * nkb * kImgBlk;
+  if (img && img_bytes >= bytesA + bytesB && p > kN) {
     // several column tiles of G would each re-slice A: slice it once (row image) and feed the tensor cores by
-    // bulk copies
+    // bulk copies, on 128 x 128 tiles
     uint8_t* imgA = img;
     uint8_t* imgB = img + bytesA;
     oz_slice_rows_kernel<<<(unsigned)((int64_t)tiles_m * nkb), 256, 0, s>>>(A, lda, n, m, Er, imgA, nkb);
-    oz_slice_kernel<64><<<(unsigned)(tiles_n * nkb), 256, 0, s>>>(G, ldg, m, p, Fc, imgB, nkb);
+    oz_slice_kernel<128><<<(unsigned)(tiles_n * nkb), 256, 0, s>>>(G, ldg, m, p, Fc, imgB, nkb);
     count_launch(2);
     e = prep_img((const void*)oz_img_kernel<true>);
     if (e != cudaSuccess) return e;
