@@ -499,10 +499,13 @@ oz_update_kernel(const double* __restrict__ A, int64_t lda, const double* __rest
 // both operands), pass 1 groups g = 4..7 (all planes), each in 4 accumulators of 128 columns (all 512 TMEM
 // columns), and each pass is folded at the chunk's end. Against 128 x 64 tiles with all 8 groups resident, every
 // MMA is twice as wide, so the tensor cores read half as many operand bytes from shared memory per product.
+// A buffer holds one pass-1 stage (all 8 planes of both operands, 26 MMAs) or two pass-0 stages (planes 0..3, 20
+// MMAs), so that every wait on a buffer is followed by at least 20 MMAs.
 constexpr int kSK = 16;                                   // K per stage
 constexpr uint32_t kSSBO = (kSK / 8) * 128;              // 256 B between 8-row groups
 constexpr uint32_t kSAPlane = (128 / 8) * kSSBO;         // 4 KB: one 128-row plane
 constexpr uint32_t kImgBlk = kDig * kSAPlane;            // 32 KB: the 8 planes of one (tile, 16-row block)
+constexpr uint32_t kHalf = kImgBlk / 2;                  // 16 KB: planes 0..3 of one (tile, 16-row block)
 constexpr uint32_t kStage2 = 2 * kImgBlk;                // 64 KB: both operands, all planes
 constexpr int kSBuf = 3;
 constexpr int kN2 = 128;                                 // output columns per tile of the image-fed product
@@ -601,7 +604,6 @@ __global__ void __launch_bounds__(kThreads, 1) oz_img_kernel(ImgArgs a) {
   const int kb0 = blockIdx.y * a.kb_per_split;
   const int kb1 = min(a.nkb, kb0 + a.kb_per_split);
   const int nst = kb1 > kb0 ? kb1 - kb0 : 0;
-  const int nit = 2 * nst;                        // stage items: every stage once per pass
   const int tid = threadIdx.x;
   for (int i = tid; i < kM; i += kThreads) sm.Ea[i] = (m0 + i < a.ma) ? a.Ea[m0 + i] : kNoExp;
   for (int i = tid; i < kN2; i += kThreads) sm.Eb[i] = (n0 + i < a.mb) ? a.Eb[n0 + i] : kNoExp;
@@ -625,29 +627,34 @@ __global__ void __launch_bounds__(kThreads, 1) oz_img_kernel(ImgArgs a) {
   const int q = warp & 3, h = warp >> 2;
   const uint8_t* srcA = a.imgA + (size_t)tm * a.nkb * kImgBlk;
   const uint8_t* srcB = a.imgB + (size_t)tn * a.nkb * kImgBlk;
-  // Item t is (pass, stage) of chunk t / (2 CB): the chunk's len stages in pass 0, then the same stages in pass 1
-  // (CB = kSChunkBlocks; the last chunk may be shorter). Pass 0 needs digit planes 0..3 of both operands, pass 1 all
-  // 8. Thread 0 of warp 0 produces (bulk copies into a free buffer), thread 0 of warp 1 consumes (MMAs, then a
-  // commit that frees the buffer); both run ahead independently within a (chunk, pass) block, and all warps meet at
-  // its end to fold its 4 group accumulators. issued / consumed live in shared memory for the timeout path.
-  auto item = [&](int t, int& pass, int& st) {
-    const int ci = t / (2 * kSChunkBlocks);
-    const int c0 = ci * kSChunkBlocks;
-    const int len = min(kSChunkBlocks, nst - c0);
-    const int r = t - 2 * kSChunkBlocks * ci;
-    pass = r >= len ? 1 : 0;
-    st = c0 + r - pass * len;
-  };
+  // Items fill buffers in consumption order. Chunk ci (CB = kSChunkBlocks stages, the last chunk possibly shorter,
+  // len stages) takes ceil(len / 2) pass-0 items, each the low planes of two stages, then len pass-1 items, one
+  // stage each. Thread 0 of warp 0 produces (bulk copies into a free buffer), thread 0 of warp 1 consumes (MMAs,
+  // then a commit that frees the buffer); both run ahead independently within a (chunk, pass) block, and all warps
+  // meet at its end to fold its 4 group accumulators. issued / consumed live in shared memory for the timeout path.
+  constexpr int kCI = kSChunkBlocks / 2 + kSChunkBlocks;   // items of a full chunk
+  const int nchunk = (int)ceil_div(nst, kSChunkBlocks);
+  const int last_len = nst - (nchunk - 1) * kSChunkBlocks;
+  const int nit = nchunk == 0 ? 0 : (nchunk - 1) * kCI + (last_len + 1) / 2 + last_len;
   auto issue = [&](int t) {                       // item t into buffer t % kSBuf
-    int pass, st;
-    item(t, pass, st);
+    const int ci = t / kCI, c0 = ci * kSChunkBlocks;
+    const int len = min(kSChunkBlocks, nst - c0), n0 = (len + 1) / 2, r = t - kCI * ci;
     const int b = t % kSBuf;
     const uint32_t dst = smem_u32(dyn + b * kStage2);
     const uint32_t fb = smem_u32(&sm.full[b]);
-    const uint32_t bytes = pass ? kImgBlk : kImgBlk / 2;      // planes 0..7 or 0..3 of each operand
-    mbar_expect_tx(fb, 2 * bytes);
-    bulk_g2s(dst, srcA + (size_t)(kb0 + st) * kImgBlk, bytes, fb);
-    bulk_g2s(dst + kImgBlk, srcB + (size_t)(kb0 + st) * kImgBlk, bytes, fb);
+    if (r < n0) {                                 // pass 0: planes 0..3 of stages c0 + 2 r (and c0 + 2 r + 1)
+      const int st = c0 + 2 * r, ns = min(2, c0 + len - st);
+      mbar_expect_tx(fb, 2u * (uint32_t)ns * kHalf);
+      for (int u = 0; u < ns; ++u) {
+        bulk_g2s(dst + u * kHalf, srcA + (size_t)(kb0 + st + u) * kImgBlk, kHalf, fb);
+        bulk_g2s(dst + kImgBlk + u * kHalf, srcB + (size_t)(kb0 + st + u) * kImgBlk, kHalf, fb);
+      }
+    } else {                                      // pass 1: all planes of stage c0 + r - n0
+      const int st = c0 + r - n0;
+      mbar_expect_tx(fb, 2 * kImgBlk);
+      bulk_g2s(dst, srcA + (size_t)(kb0 + st) * kImgBlk, kImgBlk, fb);
+      bulk_g2s(dst + kImgBlk, srcB + (size_t)(kb0 + st) * kImgBlk, kImgBlk, fb);
+    }
   };
   float hi[64], lo[64];
 #pragma unroll
@@ -655,11 +662,10 @@ __global__ void __launch_bounds__(kThreads, 1) oz_img_kernel(ImgArgs a) {
   constexpr uint32_t idesc = idesc_bf16(kM, kN2);
   bool ok = true;
   int issued = 0, consumed = 0;                   // thread 0 / thread 32 only
-  const int nchunk = (int)ceil_div(nst, kSChunkBlocks);
   for (int ci = 0; ci < nchunk && ok; ++ci) {
-    const int len = min(kSChunkBlocks, nst - ci * kSChunkBlocks);
+    const int len = min(kSChunkBlocks, nst - ci * kSChunkBlocks), n0 = (len + 1) / 2;
     for (int pass = 0; pass < 2; ++pass) {
-      const int tb0 = 2 * kSChunkBlocks * ci + pass * len, tb1 = tb0 + len;
+      const int tb0 = kCI * ci + (pass ? n0 : 0), tb1 = tb0 + (pass ? len : n0);
       if (tid == 0) {
         // keep up to kSBuf items in flight: this block's and the first ones of the next
         const int upto = min(nit, tb1 + kSBuf - 1);
@@ -682,12 +688,26 @@ __global__ void __launch_bounds__(kThreads, 1) oz_img_kernel(ImgArgs a) {
           tc_fence_after();
           const uint32_t a0 = smem_u32(dyn + b * kStage2), b0 = a0 + kImgBlk;
           const bool first = t == tb0;
+          if (pass == 0) {
+            const int ns = min(2, len - 2 * (t - tb0));
+            for (int u = 0; u < ns; ++u) {
 #pragma unroll
-          for (int gl = 0; gl < 4; ++gl) {
-            const int g = 4 * pass + gl;
-            for (int j = 0; j <= g; ++j) {           // digit pairs (j, g - j), both at most 7 since g <= 7
-              mma_bf16(tmem + (uint32_t)(gl * kN2), smem_desc_nosw(a0 + j * kSAPlane, 128, kSSBO),
-                       smem_desc_nosw(b0 + (g - j) * kSAPlane, 128, kSSBO), idesc, (first && j == 0) ? 0u : 1u);
+              for (int g = 0; g < 4; ++g) {
+                for (int j = 0; j <= g; ++j) {       // digit pairs (j, g - j), planes 0..3
+                  mma_bf16(tmem + (uint32_t)(g * kN2), smem_desc_nosw(a0 + u * kHalf + j * kSAPlane, 128, kSSBO),
+                           smem_desc_nosw(b0 + u * kHalf + (g - j) * kSAPlane, 128, kSSBO), idesc,
+                           (first && u == 0 && j == 0) ? 0u : 1u);
+                }
+              }
+            }
+          } else {
+#pragma unroll
+            for (int gl = 0; gl < 4; ++gl) {
+              const int g = 4 + gl;
+              for (int j = 0; j <= g; ++j) {         // digit pairs (j, g - j), both at most 7 since g <= 7
+                mma_bf16(tmem + (uint32_t)(gl * kN2), smem_desc_nosw(a0 + j * kSAPlane, 128, kSSBO),
+                         smem_desc_nosw(b0 + (g - j) * kSAPlane, 128, kSSBO), idesc, (first && j == 0) ? 0u : 1u);
+              }
             }
           }
           mma_commit(smem_u32(&sm.empty[b]));
