@@ -508,7 +508,7 @@ def main():
                 "parity": parity_of(lam, res, stats, gold), "history": stats[-1]["history"],
                 "counts": {k_: stats[-1][k_] for k_ in ("n_rr", "n_drop_p", "n_cholqr_fallback", "n_polar",
                                                          "n_orth_skip", "n_eig_diagonal", "n_eig_refined",
-                                                         "n_eig_mixed", "n_locked")}}
+                                                         "n_eig_mixed", "n_rr_unit", "n_locked")}}
 
     def phase_solve(form, maxiter):
         s = solver(form, maxiter=maxiter, timing=True)

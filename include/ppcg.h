@@ -115,6 +115,8 @@ typedef struct {
   int32_t n_eig_refined;      /* Rayleigh-Ritz eigensolves finished by eigenvector refinement from the identity */
   int32_t n_eig_mixed;        /* Rayleigh-Ritz eigensolves by single-precision Jacobi + FP64 eigenvector refinement
                                  (the others that are not diagonal, refined or mixed took FP64 Jacobi) */
+  int32_t n_rr_unit;          /* Rayleigh-Ritz steps with locked columns whose eigenvectors were unit vectors: the
+                                 locked columns and H applied to them were copied, only the active ones computed */
 } ppcg_stats;
 
 typedef struct ppcg_ctx* ppcg_handle;

@@ -49,7 +49,8 @@ class ppcg_stats(ctypes.Structure):
                 ("n_early_rr", ctypes.c_int32), ("converged", ctypes.c_int32), ("history_len", ctypes.c_int32),
                 ("jacobi_sweeps_max", ctypes.c_int32), ("kernel_launches", ctypes.c_int64), ("t_phase_ms", ctypes.c_double * 8),
                 ("max_res", ctypes.c_double), ("n_orth_skip", ctypes.c_int32), ("n_polar", ctypes.c_int32),
-                ("n_eig_diagonal", ctypes.c_int32), ("n_eig_refined", ctypes.c_int32), ("n_eig_mixed", ctypes.c_int32)]
+                ("n_eig_diagonal", ctypes.c_int32), ("n_eig_refined", ctypes.c_int32), ("n_eig_mixed", ctypes.c_int32),
+                ("n_rr_unit", ctypes.c_int32)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "t_phase_ms"}

@@ -509,6 +509,7 @@ ppcg_status rr_step(ppcg_ctx* c, SolveState& st, bool allow_compact, ppcg_stats*
   // sigma = smallest Ritz value of this step: the host needs it for the preconditioner
   CK(cudaMemcpyAsync(c->lam_h.data(), c->lam, sizeof(double) * kt, cudaMemcpyDeviceToHost, s));
   int fl[3] = {0, 0, 0};
+  bool diag_shortcut = false;
   CK(cudaMemcpyAsync(&fl[0], c->iflag, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&fl[1], c->tcflag, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&fl[2], rrflag, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -527,14 +528,34 @@ ppcg_status rr_step(ppcg_ctx* c, SolveState& st, bool allow_compact, ppcg_stats*
     CK(cudaMemcpyAsync(&fl[0], c->iflag, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (fl[0] & kFlagTimeout) return PPCG_ERR_TIMEOUT;
+  } else if (kl > 0 && c->eig_path == 1) {
+    // The eigenvectors are unit vectors (K was diagonal to the eigensolver's tolerance) and so are the locked
+    // columns of R^{-1} = [[I, -U], [0, Ra^{-1}]]: the new block S R^{-1} Z is [X_lock, S R^{-1}[:, kl:]] with its
+    // columns permuted by Z. The locked columns, and H applied to them, are copied instead of recomputed.
+    const int ka = kt - kl;
+    PS(update(c, c->X, c->ld, c->Rinv + (int64_t)kl * kt, kt, kt, ka, c->Xs + (int64_t)kl * c->ld, c->ld, Epi::Store,
+              false));
+    CK(cudaMemcpy2DAsync(c->Xs, c->ld * sizeof(double), c->X, c->ld * sizeof(double), c->n * sizeof(double), kl,
+                         cudaMemcpyDeviceToDevice, s));
+    phase_mark(c, PPCG_T_AX);
+    PS(apply_H(c, c->Xs + (int64_t)kl * c->ld, c->ld, c->HX + (int64_t)kl * c->ld, c->ld, ka));
+    phase_mark(c, PPCG_T_RR);
+    CK(unit_column_rows(c->C, kt, c->idx, s));
+    CK(gather_cols(c->Xs, c->ld, c->X, c->ld, c->n, c->idx, kt, s));
+    CK(gather_cols(c->HX, c->ld, c->Xs, c->ld, c->n, c->idx, kt, s));
+    swap(c->HX, c->Xs);
+    diag_shortcut = true;
+    if (stats) stats->n_rr_unit++;
   } else {
     // coefficients R^{-1} Z (R^{-1} is upper triangular)
     CK(kxk_gemm(kxk(c), false, c->Rinv, kt, c->C, kt, kt, kt, kt, c->G, kt, s));
   }
-  PS(update(c, c->X, c->ld, c->G, kt, kt, kt, c->Xs, c->ld, Epi::Store, false));
-  swap(c->X, c->Xs);
-  phase_mark(c, PPCG_T_AX);
-  PS(apply_H(c, c->X, c->ld, c->HX, c->ld, kt));
+  if (!diag_shortcut) {
+    PS(update(c, c->X, c->ld, c->G, kt, kt, kt, c->Xs, c->ld, Epi::Store, false));
+    swap(c->X, c->Xs);
+    phase_mark(c, PPCG_T_AX);
+    PS(apply_H(c, c->X, c->ld, c->HX, c->ld, kt));
+  }
   phase_mark(c, PPCG_T_PRECOND);
   st.sigma = c->lam_h[0];
   if (stats) {

@@ -120,6 +120,8 @@ cudaError_t reduce_colnorms(const double* norm_part, int64_t tiles, int m, doubl
 // out[:, j] = idx[j] >= 0 ? in[:, idx[j]] : 0 for j < m
 cudaError_t gather_cols(const double* in, int64_t ldi, double* out, int64_t ldo, int64_t n, const int* idx, int m,
                         cudaStream_t s);
+// rows[j] = row of the nonzero entry of column j of the m x m matrix C (column-major), whose columns are unit vectors
+cudaError_t unit_column_rows(const double* C, int m, int* rows, cudaStream_t s);
 // Unit norm and largest-modulus entry (lowest index on ties) positive, in place on n x m.
 cudaError_t normalize_phase(double* X, int64_t ld, int64_t n, int m, double* scratch, cudaStream_t s);
 // rho[p] = scale * sum_{c < k} X[p, c]^2

@@ -404,6 +404,21 @@ cudaError_t gather_cols(const double* in, int64_t ldi, double* out, int64_t ldo,
   return cudaGetLastError();
 }
 
+// rows[j] = the row of the nonzero entry of column j of an m x m matrix whose columns are unit vectors (one block
+// per column; exactly one thread writes)
+__global__ void unit_column_rows_kernel(const double* __restrict__ C, int m, int* __restrict__ rows) {
+  const int j = blockIdx.x;
+  for (int i = threadIdx.x; i < m; i += blockDim.x)
+    if (C[i + (int64_t)j * m] != 0.0) rows[j] = i;
+}
+
+cudaError_t unit_column_rows(const double* C, int m, int* rows, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  unit_column_rows_kernel<<<m, 256, 0, s>>>(C, m, rows);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t normalize_phase(double* X, int64_t ld, int64_t n, int m, double* /*scratch*/, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
   phase_kernel<<<m, 1024, 0, s>>>(X, ld, n);

@@ -216,6 +216,24 @@ def test_solve_grid16_k64_against_dense_golden():
     # late Rayleigh-Ritz matrices are diagonal or nearly so: those eigensolves skip the Jacobi sweeps
     assert st["n_eig_diagonal"] > 0 and st["n_eig_refined"] > 0, st
     assert st["n_eig_diagonal"] + st["n_eig_refined"] < st["n_rr"], st
+    # and with locked columns such a step copies the locked block instead of rotating it: the pairs above (residuals
+    # against the oracle's operator, orthonormality, the dense eigenvalues) hold with that route taken
+    assert 0 < st["n_rr_unit"] <= st["n_eig_diagonal"], st
+
+
+@pytest.mark.parametrize("fp64_gemm", ["fma", "ozaki"])
+def test_unit_eigenvector_rayleigh_ritz_steps_keep_the_locked_block(fp64_gemm):
+    # 16^3, k = 64: the Rayleigh-Ritz steps whose eigenvectors are unit vectors take the copy route; the solve still
+    # matches the dense eigenvalues, and the returned block is orthonormal to FP64 accuracy
+    w = wl.GRID16_K64
+    V, X0 = wl.make_inputs(w)
+    gold = np.loadtxt(os.path.join(GOLDEN, "grid16_k64_dense_eigs.txt"))[:w.k]
+    lam, X, res, st = _gpu_solve(V, w.N, w.k, w.sbsize, w.rr_period, X0, tol=w.tol, maxiter=5000,
+                                 fp64_gemm=fp64_gemm)
+    assert st["converged"] == 1, st
+    assert st["n_rr_unit"] > 0, st
+    assert np.all(_rel(lam, gold) <= LAM_TOL), np.max(_rel(lam, gold))
+    _check_pairs(V, w.N, lam, X, w.tol)
 
 
 def test_solve_grid32_k256_full_size():
