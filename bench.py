@@ -309,7 +309,7 @@ def cpu_baseline(w, trajectory, label, V=None, X0=None):
     t0 = time.perf_counter()
     t = model.measure()
     sampled = time.perf_counter() - t0
-    kt = w.k
+    kt = w.k + w.nbuf
     value = OracleCost.predict(t, trajectory, kt)
     iters = sum(1 for it, _, _ in trajectory if it > 0)
     cores = _host_cores()
@@ -341,7 +341,7 @@ def run_reference(args, w):
         step_s.append(time.perf_counter() - t0)
     t = {nm: statistics.median(v) for nm, v in samples.items()}
     traj = reference_trajectory(w)
-    value = OracleCost.predict(t, traj, w.k)
+    value = OracleCost.predict(t, traj, w.k + w.nbuf)
     iters = sum(1 for it, _, _ in traj if it > 0)
     cores = _host_cores()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -364,17 +364,17 @@ def reference_trajectory(w):
     """Trajectory for the reference arm: the stored run-length summary for the 48^3 workload, else (smaller
     workloads) the oracle's own full run, which finishes in minutes there."""
     if w.name == wl.GRID48_K1024.name and TRAJECTORY_GRID48:
-        return trajectory_expand(TRAJECTORY_GRID48, w.k)
+        return trajectory_expand(TRAJECTORY_GRID48, w.k + w.nbuf)
     import oracle
     V, X0 = wl.make_inputs(w)
-    r = oracle.ppcg(V, w.N, w.h, w.k, w.sbsize, w.rr_period, X0, tol=w.tol, maxiter=6000,
+    r = oracle.ppcg(V, w.N, w.h, w.k, w.sbsize, w.rr_period, X0, tol=w.tol, maxiter=6000, nbuf=w.nbuf,
                     theta=w.theta if w.dtype == "c128" else None)
-    return oracle_trajectory(r.history, w.k)
+    return oracle_trajectory(r.history, w.k + w.nbuf)
 
 
 def workload_config(w, form):
     return {"workload": w.name, "n": w.n, "k": w.k, "sbsize": w.sbsize, "rr_period": w.rr_period, "tol": w.tol,
-            "form": form,
+            "nbuf": w.nbuf, "form": form,
             "potential": (f"{w.n_wells} Gaussian wells + U[0,0.1) noise" if w.potential == "wells"
                           else "V ~ U[0,1)"),
             "operator": (f"complex Bloch twist {w.theta}, solved in the real form of order 2n"
@@ -394,7 +394,10 @@ FORMS = {
     "fp64_ozaki_polar": ("fp64", "ozaki", "polar"),
     "mixed_ozaki_polar": ("mixed_tf32", "ozaki", "polar"),
     "mixed_bf16_ozaki": ("mixed_bf16", "ozaki", "cholqr2"),
+    "mixed_ozaki_nbuf0": ("mixed_tf32", "ozaki", "cholqr2"),
 }
+# forms that override the workload's number of buffer vectors
+FORM_NBUF = {"mixed_ozaki_nbuf0": 0}
 FORM_TEXT = {
     "fp64": "FP64 throughout (FP64 FMA pipe GEMMs), CholeskyQR2",
     "mixed": "TF32 tcgen05 projection GEMMs and first CholeskyQR Gram; the other GEMMs on the FP64 FMA pipe",
@@ -405,6 +408,7 @@ FORM_TEXT = {
     "mixed_ozaki_polar": "mixed_ozaki with the polar-series orthonormalisation of Section 5.5",
     "mixed_bf16_ozaki": "mixed with BF16 tcgen05 projections and first CholeskyQR Gram (FP32 accumulation), the "
                         "other FP64 n x k GEMMs emulated on BF16 tcgen05 (Ozaki)",
+    "mixed_ozaki_nbuf0": "mixed_ozaki without buffer vectors (X has exactly k columns)",
 }
 # the FP64-accurate tensor-core form whose full solve stands in for each windowed form's iteration count
 WINDOW_PARTNER = {"fp64": "fp64_ozaki", "mixed": "mixed_ozaki"}
@@ -421,7 +425,7 @@ def main():
                          "grid48_k512_bloch, grid32_k128_bloch (the complex Bloch recipe), batch64 (64 uneven "
                          "problems)")
     ap.add_argument("--maxiter", type=int, default=6000)
-    ap.add_argument("--forms", default="mixed_ozaki,fp64_ozaki,mixed_bf16_ozaki",
+    ap.add_argument("--forms", default="mixed_ozaki,fp64_ozaki,mixed_bf16_ozaki,mixed_ozaki_nbuf0",
                     help="forms solved to tolerance; the first is the headline value (" + ", ".join(FORMS) + ")")
     ap.add_argument("--form-repeats", type=int, default=2, help="timed solves of each non-headline form")
     ap.add_argument("--window-forms", default="fp64,mixed",
@@ -465,7 +469,14 @@ def main():
     stream = torch.cuda.current_stream(dev)
     V, X0 = wl.make_inputs(w)
     V_d = torch.from_numpy(V).to(dev)
-    X0_d = torch.from_numpy(np.ascontiguousarray(X0.T)).to(dev)         # (k, n) rows = columns of X0
+    X0_d = torch.from_numpy(np.ascontiguousarray(X0.T)).to(dev)         # (k + nbuf, n) rows = columns of X0
+    X0_by_nbuf = {w.nbuf: X0_d}
+
+    def start(form):
+        nb = FORM_NBUF.get(form, w.nbuf)
+        if nb not in X0_by_nbuf:
+            X0_by_nbuf[nb] = torch.from_numpy(np.ascontiguousarray(wl.make_inputs(w, ncols=w.k + nb)[1].T)).to(dev)
+        return X0_by_nbuf[nb]
     gold = stored_eigs(w)
     cplx = w.dtype == "c128"
     sk = {"dtype": w.dtype, "theta": w.theta} if cplx else {}          # Solver arguments of the operator
@@ -476,13 +487,14 @@ def main():
     def solver(form, **kw):
         prec, gm, orth = FORMS[form]
         return pk.Solver(V_d, w.N, w.k, w.sbsize, rr_period=w.rr_period, device=dev, stream=stream, precision=prec,
-                         fp64_gemm=gm, orth=orth, **sk, **kw)
+                         fp64_gemm=gm, orth=orth, nbuf=FORM_NBUF.get(form, w.nbuf), **sk, **kw)
 
     def run_form(form, steps, warmup, clk_sampler):
         s = solver(form, maxiter=args.maxiter, history=args.maxiter + 8)
         X_out = torch.empty((w.k, w.n), dtype=s.dtype, device=dev)
+        X0_f = start(form)
         for _ in range(warmup):
-            s.solve(X0_d, w.tol, out=X_out)
+            s.solve(X0_f, w.tol, out=X_out)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         iters, launches, stats = 0, 0, []
         if dist:
@@ -492,7 +504,7 @@ def main():
             ev0.record(stream)
             t0 = time.perf_counter()
             for _ in range(steps):
-                lam, _, res, st = s.solve(X0_d, w.tol, out=X_out)
+                lam, _, res, st = s.solve(X0_f, w.tol, out=X_out)
                 iters += st["iters"]
                 launches += st["kernel_launches"]
                 stats.append(st)
@@ -512,7 +524,7 @@ def main():
 
     def phase_solve(form, maxiter):
         s = solver(form, maxiter=maxiter, timing=True)
-        _, _, _, st = s.solve(X0_d, w.tol)
+        _, _, _, st = s.solve(start(form), w.tol)
         s.close()
         return {k_: round(v_, 2) for k_, v_ in st["t_phase_ms"].items()}, st
 
@@ -538,7 +550,7 @@ def main():
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(stream)
-            _, _, _, st = s.solve(X0_d, w.tol)
+            _, _, _, st = s.solve(start(g), w.tol)
             e1.record(stream)
             torch.cuda.synchronize()
             s.close()
@@ -620,7 +632,7 @@ def separable_parity(pk, w, dev, stream, form, maxiter):
     spectrum (the wells workload has no independent reference at this size)."""
     import torch
     sw = wl.Workload(w.name.replace(f"wells{w.n_wells}", "separable"), N=w.N, k=w.k, sbsize=w.sbsize,
-                     rr_period=w.rr_period, potential="separable", seed=w.seed + 100)
+                     rr_period=w.rr_period, potential="separable", seed=w.seed + 100, nbuf=w.nbuf)
     V, X0 = wl.make_inputs(sw)
     N = w.N
     Vg = V.reshape((N, N, N), order="F")
@@ -628,7 +640,7 @@ def separable_parity(pk, w, dev, stream, form, maxiter):
                             N, w.k)
     prec, gm, orth = FORMS[form]
     s = pk.Solver(torch.from_numpy(V).to(dev), N, w.k, w.sbsize, rr_period=w.rr_period, device=dev, stream=stream,
-                  precision=prec, fp64_gemm=gm, orth=orth, maxiter=maxiter)
+                  precision=prec, fp64_gemm=gm, orth=orth, maxiter=maxiter, nbuf=sw.nbuf)
     t0 = time.perf_counter()
     lam, _, res, st = s.solve(torch.from_numpy(np.ascontiguousarray(X0.T)).to(dev), w.tol)
     el = time.perf_counter() - t0
@@ -912,6 +924,7 @@ def run_e2e(pk, w, V, X0, steps, stream, form):
     op = pk.ppcg_operator(w.N, w.N, w.N, w.h, Vh.data_ptr(), (ctypes.c_double * 3)(*w.theta), 1 if cplx else 0)
     opt = pk.ppcg_options()
     opt.maxiter = 6000
+    opt.nbuf = w.nbuf
     prec, gm, orth = form
     opt.precision = {"fp64": 0, "mixed_tf32": 1, "mixed_bf16": 2}[prec]
     opt.fp64_gemm = {"fma": 0, "ozaki": 1}[gm]
@@ -928,7 +941,8 @@ def run_e2e(pk, w, V, X0, steps, stream, form):
     finally:
         pk.ppcg_destroy(h)
     es = 16 if cplx else 8
-    return {"value": el, "unit": "s", "h2d_bytes_per_step": 8 * n + es * n * k, "d2h_bytes_per_step": es * n * k + 16 * k,
+    return {"value": el, "unit": "s", "h2d_bytes_per_step": 8 * n + es * n * (k + w.nbuf),
+            "d2h_bytes_per_step": es * n * k + 16 * k,
             "steps": steps, "max_residual": float(np.max(res))}
 
 

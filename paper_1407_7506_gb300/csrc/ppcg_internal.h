@@ -17,7 +17,8 @@ constexpr double kJacobiTol = 1e-14;    // k x k Jacobi: rotate while |a_pq| > k
 constexpr double kJacobiTolSmall = 1e-16;  // sub-block warp Jacobi
 constexpr int kJacobiMaxSweeps = 60;
 constexpr double kRefineTau = 1e-4;      // refine from the identity when max |M_ij| (i != j) <= kRefineTau ||M||_F
-constexpr int kRefineSteps = 4;          // refinement steps before falling back to Jacobi
+constexpr int kRefineSteps = 6;          // refinement steps before falling back to Jacobi (the correction roughly
+                                         // squares per step: from an FP32 Jacobi start, 1e-1 .. 1e-2 takes 5)
 constexpr double kRefineAccept = 1e-8;   // accept a refinement step whose largest |E_ij| (i != j) is at most this
 constexpr double kJacobiTol32 = 3e-7;    // single-precision Jacobi (start of the refinement): rotate while
                                          // |a_pq| > kJacobiTol32 ||A||_F

@@ -43,6 +43,7 @@ class Workload:
     dtype: str = "f64"     # "f64" real symmetric, "c128" complex Hermitian (Bloch)
     theta: tuple = (0.0, 0.0, 0.0)
     precision: str = "fp64"
+    nbuf: int = 0          # buffer vectors (X gets k + nbuf columns; convergence is tested on the first k)
 
     @property
     def n(self) -> int:
@@ -54,8 +55,9 @@ class Workload:
 # defined at smaller sizes: 48^3 with k = 512 and 32^3 with k = 128). The batched set is batch() below.
 GRID16_K64 = Workload("grid16_k64_q1_uniform", N=16, k=64, sbsize=1, potential="uniform", seed=1001)
 GRID32_K256 = Workload("grid32_k256_q4_wells8", N=32, k=256, sbsize=4, potential="wells", n_wells=8, seed=1002)
+# nbuf = 50: the number of buffer vectors of every test in the paper's experiments (Section 6)
 GRID48_K1024 = Workload("grid48_k1024_q8_wells32", N=48, k=1024, sbsize=8, potential="wells", n_wells=32,
-                        seed=1003, precision="mixed")
+                        seed=1003, precision="mixed", nbuf=50)
 GRID64_K2048_BLOCH = Workload("grid64_k2048_q8_wells64_bloch", N=64, k=2048, sbsize=8, potential="wells",
                               n_wells=64, seed=1005, dtype="c128", theta=(0.3, 0.7, 1.1))
 # the Bloch recipe at 48^3 with k = 512 and sbsize = 8: the wells keep the 64^3 recipe's density (64 x (48/64)^3 = 27)
@@ -112,8 +114,8 @@ def potential(w: Workload, rng: np.random.Generator) -> np.ndarray:
 
 
 def start_block(w: Workload, rng: np.random.Generator, ncols: int | None = None) -> np.ndarray:
-    """Draw X0 (n x ncols, column-major) for workload w from rng."""
-    ncols = w.k if ncols is None else ncols
+    """Draw X0 (n x ncols, column-major; by default k + nbuf columns) for workload w from rng."""
+    ncols = w.k + w.nbuf if ncols is None else ncols
     if w.dtype == "c128":
         re = rng.standard_normal((w.n, ncols))
         im = rng.standard_normal((w.n, ncols))
