@@ -225,9 +225,11 @@ class OracleCost:
         """trajectory: (iteration, kind, k_act) per iteration after the start (kind 0 plain, 1 Rayleigh-Ritz),
         iteration 0 being the initial Rayleigh-Ritz step."""
         total = t["orth"] + t["rr"]
+        prev = None
         for it, kind, ka in trajectory:
-            if it == 0:
+            if it == 0 or it == prev:                             # the history repeats the final step's entry
                 continue
+            prev = it
             a = ka / kt
             total += (t["precond"] + t["blocks"]) * a + t["project"] * a * (1 if it == 1 else 2)
             total += t["copy"] * (kt - ka) / kt                   # X_lock = X[:, J_lock] at every iteration
@@ -249,23 +251,19 @@ def oracle_trajectory(history, kt):
     return out
 
 
-# The iteration trajectory of the benchmarked 48^3 mixed-form solve, for the reference arm (which runs no GPU code):
+# The iteration trajectory of the benchmarked 48^3 mixed-form solve (k = 1024 with 50 buffer vectors), for the
+# reference arm (which runs no GPU code):
 # runs of iterations [first, last] with the same number of active columns, and the Rayleigh-Ritz iterations, as the
 # library's solve history recorded them (bench.py prints them as "trajectory"). The main arm uses the trajectory
 # of its own timed solve instead.
 TRAJECTORY_GRID48 = {
-    "runs": [(1, 25, 1024), (26, 30, 1020), (31, 35, 890), (36, 40, 756), (41, 45, 648), (46, 50, 538), (51, 55, 455),
-             (56, 60, 402), (61, 65, 354), (66, 70, 306), (71, 75, 272), (76, 80, 241), (81, 85, 220), (86, 90, 192),
-             (91, 95, 179), (96, 100, 162), (101, 105, 152), (106, 110, 138), (111, 115, 131), (116, 120, 117),
-             (121, 125, 114), (126, 130, 107), (131, 135, 100), (136, 140, 90), (141, 145, 86), (146, 150, 81),
-             (151, 155, 79), (156, 160, 73), (161, 165, 71), (166, 170, 69), (171, 175, 63), (176, 180, 59),
-             (181, 185, 55), (186, 190, 51), (191, 195, 50), (196, 200, 46), (201, 210, 43), (211, 215, 40),
-             (216, 220, 37), (221, 225, 31), (226, 230, 30), (231, 245, 28), (246, 250, 26), (251, 255, 23),
-             (256, 260, 22), (261, 265, 21), (266, 275, 20), (276, 280, 19), (281, 285, 18), (286, 295, 17),
-             (296, 305, 16), (306, 310, 15), (311, 320, 14), (321, 325, 12), (326, 330, 11), (331, 340, 10),
-             (341, 355, 9), (356, 365, 6), (366, 410, 5), (411, 440, 4), (441, 550, 3), (551, 690, 2), (691, 1209, 1),
-             (1209, 1209, 1)],
-    "rr": sorted(set(range(5, 1210, 5)) | {1209}),
+    "runs": [(1, 25, 1074), (26, 30, 1069), (31, 35, 929), (36, 40, 796), (41, 45, 683), (46, 50, 573),
+             (51, 55, 479), (56, 60, 426), (61, 65, 369), (66, 70, 325), (71, 75, 294), (76, 80, 255), (81, 85, 231),
+             (86, 90, 211), (91, 95, 189), (96, 100, 174), (101, 105, 161), (106, 110, 149), (111, 115, 140),
+             (116, 120, 126), (121, 125, 117), (126, 130, 105), (131, 135, 97), (136, 140, 90), (141, 145, 82),
+             (146, 150, 76), (151, 155, 73), (156, 160, 68), (161, 165, 64), (166, 170, 57), (171, 175, 55),
+             (176, 182, 51), (182, 182, 51)],
+    "rr": sorted(set(range(5, 181, 5)) | {182}),
 }
 
 

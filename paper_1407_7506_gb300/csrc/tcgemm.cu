@@ -518,14 +518,20 @@ cudaError_t tc_gram(const double* A, int64_t lda, const double* B, int64_t ldb, 
   const int BK = bf16 ? kbk<true>() : kbk<false>();
   const int tiles_m = (int)ceil_div(ma, kM * MT), tiles_n = (int)ceil_div(mb, NT);
   const int tiles = tiles_m * tiles_n;
-  // one wave of CTAs, while the FP32 partials (written, then read by the reduce; mostly L2-resident) stay below
-  // half of the input bytes
-  int64_t nsplit = ceil_div((int64_t)sm_count(), tiles);
+  // The K split: the smallest whose waves per unit of K work come within 3% of the fewest (a CTA holds all of its
+  // SM's TMEM when MT NT = 512, so one CTA per SM is resident; otherwise 512 / (MT NT)), while the FP32 partials
+  // (written, then read by the reduce; mostly L2-resident) stay below half of the input bytes
   const int64_t cap_traffic = (n * (int64_t)(ma + mb)) / (2LL * ma * mb) + 1;
   const int64_t cap_rows = ceil_div(n, 4 * BK);
   const int64_t cap_mem = (int64_t)(2 * part_capacity / ((size_t)ma * mb));   // FP32 partials in FP64 space
-  nsplit = std::min(nsplit, std::min(cap_traffic, std::min(cap_rows, cap_mem)));
-  if (nsplit < 1) nsplit = 1;
+  const int64_t cap = std::max<int64_t>(1, std::min(cap_traffic, std::min(cap_rows, cap_mem)));
+  const int64_t slots = (int64_t)sm_count() * std::max(1, 512 / (NT * MT));
+  const int64_t ns_max = std::min<int64_t>(cap, 4 * slots);
+  auto cost = [&](int64_t ns) { return (double)ceil_div((int64_t)tiles * ns, slots) / (double)ns; };
+  double best = cost(1);
+  for (int64_t ns = 2; ns <= ns_max; ++ns) best = std::min(best, cost(ns));
+  int64_t nsplit = 1;
+  while (nsplit < ns_max && cost(nsplit) > 1.03 * best) ++nsplit;
   const int64_t rows = ceil_div(ceil_div(n, nsplit), BK) * BK;
   const int nsp = (int)ceil_div(n, rows);
   const dim3 grid(tiles, nsp);
