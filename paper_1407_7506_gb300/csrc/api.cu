@@ -251,7 +251,7 @@ ppcg_status update(ppcg_ctx* c, const double* A, int64_t lda, const double* G, i
                    int64_t ldy, Epi mode, bool g_upper) {
   if (c->ozaki)
     CK(oz_update(A, lda, G, ldg, c->n, m, p, Y, ldy, mode, c->ozexps, c->ozimg, c->ozimg_bytes, c->tcflag,
-                 c->stream));
+                 c->stream, g_upper));
   else
     CK(gemm_nn(A, lda, G, ldg, c->n, m, p, Y, ldy, nullptr, 0, mode, g_upper, nullptr, c->stream));
   return PPCG_OK;

@@ -569,6 +569,7 @@ struct ImgArgs {
   double* out;
   int64_t ldo;
   int symmetric, mode;
+  int upper;        // update: G upper triangular, so column tile [n0, n0 + 128) needs only its rows < n0 + 128
   int* flag;
 };
 
@@ -602,7 +603,8 @@ __global__ void __launch_bounds__(kThreads, 1) oz_img_kernel(ImgArgs a) {
   const int m0 = tm * kM, n0 = tn * kN2;
   if (!UPD && a.symmetric && n0 + kN2 <= m0) return;   // entirely below the diagonal: the reduce reads only i <= j
   const int kb0 = blockIdx.y * a.kb_per_split;
-  const int kb1 = min(a.nkb, kb0 + a.kb_per_split);
+  int kb1 = min(a.nkb, kb0 + a.kb_per_split);
+  if (UPD && a.upper) kb1 = min(kb1, (n0 + kN2 + kSK - 1) / kSK);   // the rows of G below are zero in this tile
   const int nst = kb1 > kb0 ? kb1 - kb0 : 0;
   const int tid = threadIdx.x;
   for (int i = tid; i < kM; i += kThreads) sm.Ea[i] = (m0 + i < a.ma) ? a.Ea[m0 + i] : kNoExp;
@@ -890,7 +892,7 @@ cudaError_t oz_gram(const double* A, int64_t lda, const double* B, int64_t ldb, 
     }
     const int kps = (int)(cps * kSChunkBlocks);
     const int nsp = (int)ceil_div(nkb, kps);
-    const ImgArgs args{imgA, imgB, nkb, ma, mb, tiles_n2, kps, Ea, Eb, part, ma, symmetric ? 1 : 0, 0, flag};
+    const ImgArgs args{imgA, imgB, nkb, ma, mb, tiles_n2, kps, Ea, Eb, part, ma, symmetric ? 1 : 0, 0, 0, flag};
     oz_img_kernel<false><<<dim3(tiles2, nsp), kThreads, smem, s>>>(args);
     count_launch();
     e = cudaGetLastError();
@@ -914,7 +916,8 @@ cudaError_t oz_gram(const double* A, int64_t lda, const double* B, int64_t ldb, 
 }
 
 cudaError_t oz_update(const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p, double* Y,
-                      int64_t ldy, Epi mode, int* exps, uint8_t* img, size_t img_bytes, int* flag, cudaStream_t s) {
+                      int64_t ldy, Epi mode, int* exps, uint8_t* img, size_t img_bytes, int* flag, cudaStream_t s,
+                      bool g_upper) {
   if (p <= 0 || n <= 0) return cudaSuccess;
   int* Er = exps;
   int* Fc = exps + n;
@@ -936,7 +939,8 @@ cudaError_t oz_update(const double* A, int64_t lda, const double* G, int ldg, in
     count_launch(2);
     e = prep_img((const void*)oz_img_kernel<true>);
     if (e != cudaSuccess) return e;
-    const ImgArgs args{imgA, imgB, nkb, (int)n, p, tiles_n, nkb, Er, Fc, Y, ldy, 0, (int)mode, flag};
+    const ImgArgs args{imgA, imgB, nkb, (int)n, p, tiles_n, nkb, Er, Fc, Y, ldy, 0, (int)mode, g_upper ? 1 : 0,
+                       flag};
     oz_img_kernel<true><<<dim3((unsigned)((int64_t)tiles_m * tiles_n), 1), kThreads, oz_img_smem(), s>>>(args);
     count_launch();
     return cudaGetLastError();

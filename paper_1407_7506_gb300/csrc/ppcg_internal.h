@@ -107,8 +107,11 @@ size_t oz_img_bytes(int64_t n, int cols);
 cudaError_t oz_gram(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n, int ma, int mb, double* C,
                     int ldc, bool symmetric, double* part, size_t part_capacity, int* exps, uint8_t* img,
                     size_t img_bytes, int* flag, cudaStream_t s);
+// g_upper: G is upper triangular with exact zeros below the diagonal (each column tile then reads only the rows
+// of G up to its last column; the result is the same)
 cudaError_t oz_update(const double* A, int64_t lda, const double* G, int ldg, int64_t n, int m, int p, double* Y,
-                      int64_t ldy, Epi mode, int* exps, uint8_t* img, size_t img_bytes, int* flag, cudaStream_t s);
+                      int64_t ldy, Epi mode, int* exps, uint8_t* img, size_t img_bytes, int* flag, cudaStream_t s,
+                      bool g_upper = false);
 
 // ---------------------------------------------------------------------------------------------- vectors
 // R = HX - X diag(lam); W = T R; norm_part per row tile.
