@@ -775,8 +775,8 @@ def _peaks():
 
 
 # DRAM bytes (read + write) per launch of the Ozaki image kernel (one 1024 x 1024 Gram over n = 110592), from one ncu
-# capture of that shape with the current kernel: 4.645 GB read + 13.4 MB written (profiles/oz_img_kernel_grid48_k1024.md)
-OZ_IMG_TRAFFIC_BYTES = 4.658e9
+# capture of that shape with the current kernel: 4.169 GB read + 43.7 MB written (profiles/oz_img_kernel_grid48_k1024.md)
+OZ_IMG_TRAFFIC_BYTES = 4.213e9
 
 
 def rooflines(pk, w, dev, stream, V_d, sk):
@@ -849,7 +849,7 @@ def rooflines(pk, w, dev, stream, V_d, sk):
     out["roofline_tf32_gram"] = {
         "kernel": f"tc_gram_kernel (tcgen05 TF32, + split-K reduce): X^T W, n={n}, {k}x{k}", "bound": "hbm",
         "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-        "traffic": 1.945e9 if (n, k) == (110592, 1024) else None,
+        "traffic": None,                  # the launch grid changed since the last capture (K split for whole waves)
         "algorithmic_bytes_per_launch": nbytes, "launch_ms": ms, "tflops": gemm_flops / (ms / 1e3) / 1e12,
         "peak_note": f"{kind} HBM copy bandwidth (FP64 operands read once); at k = {k} the TF32 tensor work "
                      f"({gemm_flops / 1e9:.0f} GFLOP) is within a factor of two of the byte bound"}
