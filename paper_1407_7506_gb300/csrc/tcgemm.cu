@@ -69,27 +69,22 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
 // FP32 bit pattern of the TF32 value nearest to the double whose upper 32-bit word is hi, ties away from zero (the
 // rounding of cvt.rna.tf32). The upper word holds the sign, the exponent and the leading 20 mantissa bits: the 10
 // that TF32 keeps and the first one it drops, which alone decides this rounding. The exponent is rebiased in place
-// (1023 -> 127) with integer operations only, so the conversion stays off GB300's narrow FP64 pipe. Magnitudes below
-// the FP32 normal range become zero and magnitudes above it infinity; a NaN whose payload lies only in the low word
-// becomes infinity (the result is non-finite either way).
+// (1023 -> 127) with integer operations only, so the conversion stays off GB300's narrow FP64 pipe. The magnitude is
+// first clamped to [2^-127, 2^128] (two min/max operations instead of compares and selects on the busy integer
+// pipe): below that range the result is zero, inside the FP32 subnormal range the rounded subnormal, and at or
+// above 2^128 infinity; infinities and NaNs become infinity (the result is non-finite either way).
 __device__ __forceinline__ uint32_t tf32_from_hi(uint32_t hi) {
-  const uint32_t mag = hi & 0x7FFFFFFFu;
-  uint32_t f = (((mag - 0x38000000u) << 3) + 0x1000u) & 0xFFFFE000u;
-  if (mag < 0x38100000u) f = 0u;
-  if (mag >= 0x47F00000u) f = mag > 0x7FF00000u ? 0x7FC00000u : 0x7F800000u;
-  return f | (hi & 0x80000000u);
+  const uint32_t mag = min(max(hi & 0x7FFFFFFFu, 0x38000000u), 0x47F00000u);
+  return ((((mag - 0x38000000u) << 3) + 0x1000u) & 0xFFFFE000u) | (hi & 0x80000000u);
 }
 
-// BF16 bit pattern of the value nearest to the double whose upper word is hi, ties away from zero: the same
-// integer rebias to the FP32 layout, then the FP32 pattern rounded to its upper 16 bits (8 significant bits; the
-// upper word keeps 20 mantissa bits, enough to decide this rounding). Below the FP32 normal range: zero; above it:
-// infinity (NaN stays non-finite).
+// BF16 bit pattern of the value nearest to the double whose upper word is hi, ties away from zero: the same clamp
+// and integer rebias to the FP32 layout, then the FP32 pattern rounded to its upper 16 bits (8 significant bits;
+// the upper word keeps 20 mantissa bits, enough to decide this rounding). Below 2^-127: zero; at or above 2^128,
+// and for infinities and NaNs: infinity.
 __device__ __forceinline__ uint32_t bf16_from_hi(uint32_t hi) {
-  const uint32_t mag = hi & 0x7FFFFFFFu;
-  uint32_t b = ((((mag - 0x38000000u) << 3) + 0x8000u) >> 16) & 0x7FFFu;
-  if (mag < 0x38100000u) b = 0u;
-  if (mag >= 0x47F00000u) b = mag > 0x7FF00000u ? 0x7FC0u : 0x7F80u;
-  return b | ((hi >> 16) & 0x8000u);
+  const uint32_t mag = min(max(hi & 0x7FFFFFFFu, 0x38000000u), 0x47F00000u);
+  return (((((mag - 0x38000000u) << 3) + 0x8000u) >> 16) & 0x7FFFu) | ((hi >> 16) & 0x8000u);
 }
 
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
