@@ -13,9 +13,12 @@
 // 2^(E_a + E_b - 10) per element produces the result. The error is that of the 55-bit digits plus the ~2^-48
 // relative rounding of the double-float sum, below the rounding of an FP64 GEMM of these lengths.
 //
-// Tiles: M = 128 rows (TMEM lanes) x N = 64 columns; the 8 group accumulators fill the 512 TMEM columns of an SM.
-// Operand tiles are staged by the threads (coalesced FP64 loads, integer digit extraction, BF16 stores into the
-// K-major canonical layout, 8 digit planes per operand, 2 stages); one thread issues the 72 MMAs of a stage.
+// Two forms. The register-staged kernels (narrow products, where a slice would not be re-used) take tiles of
+// M = 128 rows (TMEM lanes) x N = 64 columns, whose 8 group accumulators fill the 512 TMEM columns of an SM; their
+// operand tiles are staged by the threads (coalesced FP64 loads, integer digit extraction, BF16 stores into the
+// K-major canonical layout, 8 digit planes per operand, 2 stages) and one thread issues the 72 MMAs of a stage.
+// The image-fed product (wide operands, below) slices each operand once into digit images and runs 128 x 128
+// tiles in two passes of four group accumulators, fed by bulk copies.
 #include "ppcg_internal.h"
 #include "tc_util.cuh"
 
