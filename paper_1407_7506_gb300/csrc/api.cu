@@ -234,10 +234,12 @@ ppcg_status apply_H(ppcg_ctx* c, const double* X, int64_t ldx, double* Y, int64_
 constexpr int kProjectFuse = 128;   // W and P are projected as one block while together they have at most this many
                                     // columns (there the projections are bound by reading X, not by arithmetic)
 
-// FP64 Gram over the n grid rows: FP64 pipe, or the FP64-accurate tensor-core emulation when selected
+// FP64 Gram over the n grid rows: FP64 pipe, or the FP64-accurate tensor-core emulation when selected.
+// sym_result: A^T B is symmetric in exact arithmetic (X^T (H X) with H symmetric): only its upper tiles are formed
+// and the lower triangle mirrors them, as for A^T A.
 ppcg_status gram(ppcg_ctx* c, const double* A, int64_t lda, const double* B, int64_t ldb, int ma, int mb,
-                 double* Cm, int ldc) {
-  const bool sym = (A == B && lda == ldb && ma == mb);
+                 double* Cm, int ldc, bool sym_result = false) {
+  const bool sym = ma == mb && ((A == B && lda == ldb) || sym_result);
   if (c->ozaki)
     CK(oz_gram(A, lda, B, ldb, c->n, ma, mb, Cm, ldc, sym, c->gpart, c->gpart_cap, c->ozexps, c->ozimg,
                c->ozimg_bytes, c->tcflag, c->stream));
@@ -484,7 +486,7 @@ ppcg_status rr_step(ppcg_ctx* c, SolveState& st, bool allow_compact, ppcg_stats*
     CK(locked_gram_fill(c->G, c->M, kt, kl, c->lamlk, s));
   } else {
     PS(gram(c, c->X, c->ld, c->X, c->ld, kt, kt, c->G, kt));            // S^T S
-    PS(gram(c, c->X, c->ld, c->HX, c->ld, kt, kt, c->M, kt));           // S^T A S
+    PS(gram(c, c->X, c->ld, c->HX, c->ld, kt, kt, c->M, kt, true));     // S^T A S
   }
   CK(cudaMemsetAsync(rrflag, 0, sizeof(int), s));
   if (kl > 0) {
@@ -521,7 +523,7 @@ ppcg_status rr_step(ppcg_ctx* c, SolveState& st, bool allow_compact, ppcg_stats*
     int fb = 0;
     PS(cholqr2(c, c->X, c->ld, c->Xs, c->ld, kt, &fb));
     PS(apply_H(c, c->X, c->ld, c->HX, c->ld, kt));
-    PS(gram(c, c->X, c->ld, c->HX, c->ld, kt, kt, c->M, kt));
+    PS(gram(c, c->X, c->ld, c->HX, c->ld, kt, kt, c->M, kt, true));
     PS(dense_eigh(c, c->M, kt, c->lam, c->C));
     CK(cudaMemcpyAsync(c->G, c->C, sizeof(double) * (size_t)kt * kt, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(c->lam_h.data(), c->lam, sizeof(double) * kt, cudaMemcpyDeviceToHost, s));
@@ -869,7 +871,7 @@ ppcg_status ppcg_solve(ppcg_handle c, const double* X0, double tol, double* lamb
       phase_mark(c, PPCG_T_AX);
       PS(apply_H(c, Xa, ld, HXa, ld, ka));
       phase_mark(c, PPCG_T_GEMM);
-      PS(gram(c, Xa, ld, HXa, ld, ka, ka, c->M, ka));
+      PS(gram(c, Xa, ld, HXa, ld, ka, ka, c->M, ka, true));            // M = X^T H X
       ResidualArgs ra = resid_args(c, st.sigma);
       PS(residual_m(c, Xa, HXa, ld, ka, c->M, ra, c->W));
       CK(reduce_colnorms(c->normpart, norm_row_tiles(n), ka, c->norms, s));

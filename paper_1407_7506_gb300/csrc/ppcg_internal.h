@@ -17,12 +17,13 @@ constexpr double kJacobiTol = 1e-14;    // k x k Jacobi: rotate while |a_pq| > k
 constexpr double kJacobiTolSmall = 1e-16;  // sub-block warp Jacobi
 constexpr int kJacobiMaxSweeps = 60;
 constexpr double kRefineTau = 1e-4;      // refine from the identity when max |M_ij| (i != j) <= kRefineTau ||M||_F
-constexpr int kRefineSteps = 6;          // refinement steps before falling back to Jacobi (the correction roughly
-                                         // squares per step: from an FP32 Jacobi start, 1e-1 .. 1e-2 takes 5)
+constexpr int kRefineSteps = 8;          // refinement steps before falling back to Jacobi (the correction roughly
+                                         // squares per step: from an FP32 Jacobi start, 1e-1 .. 1e-2 takes 5-6)
 constexpr double kRefineAccept = 1e-8;   // accept a refinement step whose largest |E_ij| (i != j) is at most this
 constexpr double kJacobiTol32 = 3e-7;    // single-precision Jacobi (start of the refinement): rotate while
                                          // |a_pq| > kJacobiTol32 ||A||_F
-constexpr int kJacobiMaxSweeps32 = 10;    // its rounding floor is reached by then
+constexpr int kJacobiMaxSweeps32 = 8;     // then the refinement takes over (a random 1074 x 1074 matrix is the
+                                          // slowest case: 8 sweeps leave corrections the refinement settles)
 constexpr double kClusterGap = 4.0;      // refinement: eigenvalues closer than kClusterGap x the largest coupling
                                          // |S_ij + lam_j R_ij| form a cluster, solved as one small eigenproblem
 constexpr double kClusterFloor = 1e-7;   // ... and always those closer than kClusterFloor ||M||_F: there rounding in
